@@ -1,0 +1,159 @@
+/*
+ * ldpc.h -- C ABI of libldpc: GF(2) systematic encoding and sum-product
+ * (belief-propagation) decoding of binary LDPC codes on one GB300 GPU.
+ *
+ * Method: arXiv 2201.04265, "Distributed Processing for Encoding and
+ * Decoding of Binary LDPC codes using MPI", Sec. II (Eqs. 1-8) and the
+ * encoding/decoding procedures of Sec. III.  The paper's MPI split across
+ * CPUs is not reproduced: frames are the data-parallel axis, as in its
+ * batch processing (Sec. III-C).
+ *
+ * Conventions shared by every call
+ *   - H is m x n (m checks, n bits), given in CSR form: row_ptr[m+1] and
+ *     col_idx[nnz], column indices strictly increasing within a row.  The
+ *     position e of an entry in this CSR order is its edge index.
+ *   - Bits are packed 32 per uint32, least significant bit first; each frame
+ *     occupies whole words (NW = ceil(n/32) for codewords, KW = ceil(k/32)
+ *     for information words).  Pad bits must be 0 on input and are 0 on
+ *     output.  Codeword bits are in H's column order.
+ *   - LLRs are float32, frame-major (frame f at offset f*n), with the
+ *     paper's sign: L = ln p(bit=1)/p(bit=0), so L >= 0 decides 1 (Eqs. 4, 8).
+ *   - Pointers named d_* are device memory owned by the caller; they must
+ *     stay valid until the work queued on `stream` has finished.  Host
+ *     pointers (h_* or plain) are read before the call returns.
+ *   - Every call except create/destroy/info is asynchronous on `stream`
+ *     (NULL = the legacy default stream).  Errors in argument checking are
+ *     returned at once; an asynchronous CUDA fault surfaces as LDPC_ECUDA from
+ *     a later call or from the caller's own synchronisation.
+ *   - Return value: LDPC_OK (0) or a negative ldpc_status; no exception
+ *     crosses the ABI.  ldpc_last_error() gives a message for the calling
+ *     thread's most recent failure.
+ */
+#ifndef LDPC_GB300_H
+#define LDPC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ldpc_code ldpc_code;
+typedef struct CUstream_st *ldpc_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    LDPC_OK = 0,
+    LDPC_EINVAL = -1,   /* bad shape, pointer, degree or option */
+    LDPC_ENOMEM = -2,   /* host or device allocation failed */
+    LDPC_ECUDA = -3,    /* a CUDA call or kernel launch failed */
+    LDPC_ETIMEOUT = -4, /* a bounded wait inside a kernel gave up */
+    LDPC_ENOTSUP = -5   /* valid request outside what this build supports */
+} ldpc_status;
+
+/* Optional quasi-cyclic description: an mb x nb base matrix of circulant
+ * shifts (-1 = all-zero block) lifted by z; entry (i, j, s) connects check
+ * i*z + r to bit j*z + (r + s) mod z.  When given, row_ptr/col_idx must be
+ * NULL and n = nb*z, m = mb*z. */
+typedef struct {
+    int32_t mb, nb, z;
+    const int16_t *shift; /* host, mb*nb */
+} ldpc_qc_desc;
+
+/* flags for ldpc_code_create */
+#define LDPC_CREATE_HOST_ONLY 1u /* build host state only (no device tables);
+                                    encode/decode with such a code fail */
+
+/* Creates a code object from H (host arrays, copied).  Builds the Tanner
+ * graph edge layouts (Sec. II-B, Fig. 1) and the systematic generator
+ * (Eq. 2; Sec. III-B: G in standard form [I_k : P] after a column
+ * permutation) by GF(2) Gauss-Jordan elimination that scans pivot columns
+ * from right to left: the pivot columns are the parity positions, the other
+ * k = n - rank(H) columns the information positions, both ascending.  With
+ * H = [X | I] this puts the information bits first, as in Fig. 2.
+ * Synchronous.  Returns LDPC_EINVAL for a malformed H (n < 1, m < 1, row_ptr
+ * not monotone, a column out of range, repeated or unsorted columns in a
+ * row) or rank(H) = n. */
+int ldpc_code_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t *col_idx,
+                     const ldpc_qc_desc *qc, uint32_t flags, ldpc_code **out);
+
+/* Sizes of a code: k information bits, rank = n - k parity bits, nnz edges.
+ * Any output pointer may be NULL. */
+int ldpc_code_info(const ldpc_code *code, int32_t *n, int32_t *m, int32_t *k, int32_t *rank,
+                   int64_t *nnz);
+
+/* Host copies of the information positions (k entries) and parity positions
+ * (rank entries), both ascending.  Either pointer may be NULL. */
+int ldpc_code_positions(const ldpc_code *code, int32_t *info_pos, int32_t *parity_pos);
+
+/* Host copy of the parity map A = P^T: rank rows of KW words; bit i of row j
+ * is the coefficient of information bit i in parity bit j (Eq. 3). */
+int ldpc_code_parity_map(const ldpc_code *code, uint32_t *A);
+
+/* Frees the code; NULL is ignored.  Must not race with work still queued
+ * that uses it (synchronise the streams first). */
+void ldpc_code_destroy(ldpc_code *code);
+
+/* Systematic encoding m^T G = p^T (Eq. 3): d_info is F x KW words, d_code
+ * receives F x NW words.  Information bit i lands at info position i;
+ * parity bit j (at parity position j) is the XOR of the information bits
+ * selected by row j of A.  Every output codeword satisfies H c^T = 0
+ * (Eq. 1).  F = 0 is a no-op. */
+int ldpc_encode(const ldpc_code *code, const uint32_t *d_info, uint32_t *d_code, int32_t F,
+                ldpc_stream_t stream);
+
+/* Syndrome s = H z^T over GF(2) (Eq. 1) of F packed words d_bits (F x NW).
+ * d_syn (F x ceil(m/32) words, bit c = check c) and d_ok (F bytes, 1 when
+ * every check is satisfied) may each be NULL. */
+int ldpc_syndrome(const ldpc_code *code, const uint32_t *d_bits, int32_t F, uint32_t *d_syn,
+                  uint8_t *d_ok, ldpc_stream_t stream);
+
+/* Decoder schedules. */
+#define LDPC_SCHED_AUTO 0     /* resident when it fits on chip, else plain */
+#define LDPC_SCHED_PLAIN 1    /* flooding, messages streamed through HBM,
+                                 one check and one bit kernel per iteration */
+#define LDPC_SCHED_RESIDENT 2 /* persistent kernel, frames held in shared
+                                 memory for all iterations */
+
+typedef struct {
+    int32_t max_iters;  /* T >= 0 iterations (an iteration = all check
+                           updates, then all bit updates; Algorithm 1) */
+    int32_t early_stop; /* 1: stop a frame after the first iteration whose
+                           hard decisions satisfy H z^T = 0 */
+    int32_t msg_fp16;   /* 1: check-to-bit messages stored as binary16
+                           (computed and accumulated in FP32) */
+    int32_t schedule;   /* LDPC_SCHED_* */
+    float clip;         /* |message| clip (> 0): applied to bit-to-check
+                           inputs of the check update and to its outputs */
+} ldpc_decode_opts;
+
+/* Bytes of device workspace ldpc_decode needs for F frames of this code
+ * with these options (0 is possible). */
+int ldpc_decode_workspace_size(const ldpc_code *code, int32_t F, const ldpc_decode_opts *opts,
+                               size_t *bytes);
+
+/* Sum-product decoding of F frames (Sec. II-B, Eqs. 4-8; flooding schedule
+ * of Algorithm 1).  d_llr: F x n channel LLRs R_v.  Per iteration the check
+ * update computes E_cv = (-1)^{d_c} 2 atanh( prod_{v' != v} tanh(L_v'c/2) )
+ * (Eq. 5 with the sign its LLR convention requires) from the clipped
+ * bit-to-check messages L_vc = R_v + sum_{c' != c} E_c'v (Eq. 6), and the
+ * bit update forms L_v = R_v + sum_c E_cv (Eq. 7) and z_v = [L_v >= 0]
+ * (Eq. 8).  Outputs (each may be NULL): d_post F x n total LLRs of the last
+ * iteration performed, d_hard F x NW packed z, d_iters F iteration counts,
+ * d_ok F flags (1 when H z^T = 0).  d_work must hold
+ * ldpc_decode_workspace_size() bytes, 256-byte aligned. */
+int ldpc_decode(const ldpc_code *code, const float *d_llr, int32_t F,
+                const ldpc_decode_opts *opts, float *d_post, uint32_t *d_hard, int32_t *d_iters,
+                uint8_t *d_ok, void *d_work, size_t work_bytes, ldpc_stream_t stream);
+
+/* Status code to a static string. */
+const char *ldpc_status_string(int status);
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+const char *ldpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_GB300_H */

@@ -3,7 +3,7 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
 library: the arithmetic lives in ``ldpc_oracle.c`` (compiled with gcc by
-``oracle.build``), the brute-force references in ``brute.py`` and the FP64
+``oracle.compile``), the brute-force references in ``brute.py`` and the FP64
 weighted-BP gradient in ``wbp_ref.py``.
 
 Each wrapper cites the passage of arXiv 2201.04265 it follows; see the C file
@@ -18,7 +18,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .build import build, library_path
+from .compile import build, library_path
 
 _lib = None
 

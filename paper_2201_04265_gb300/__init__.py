@@ -1,0 +1,216 @@
+"""LDPC encoding and sum-product decoding on GB300 (arXiv 2201.04265, Secs. II-III).
+
+Thin Python binding over libldpc.so: every step of encoding and decoding runs
+in the library's CUDA kernels; this module only marshals torch tensors
+(device memory and streams) into the C ABI of include/ldpc.h.
+
+Packed bit tensors use dtype torch.int32 (the bit pattern of the ABI's
+uint32 words, LSB first).
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import DecodeOpts, LdpcError, QcDesc, c_i32, c_i64, c_vp
+
+SCHED_AUTO, SCHED_PLAIN, SCHED_RESIDENT = 0, 1, 2
+_SCHED = {"auto": SCHED_AUTO, "plain": SCHED_PLAIN, "resident": SCHED_RESIDENT}
+
+__all__ = ["Code", "encode", "syndrome", "decode", "decode_workspace_size", "DecodeResult",
+           "LdpcError", "SCHED_AUTO", "SCHED_PLAIN", "SCHED_RESIDENT"]
+
+
+def _stream_handle(stream) -> c_vp:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_vp(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> c_vp:
+    if t is None:
+        return c_vp(None)
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return c_vp(t.data_ptr())
+
+
+class Code:
+    """A code object owned by the library (Eq. 2 generator and Tanner-graph layouts).
+
+    ``Code(n, m, row_ptr, col_idx)`` takes H in CSR form (host arrays), or
+    ``Code.from_qc(base, z)`` a quasi-cyclic base matrix.  The object lives on
+    the CUDA device current at creation unless ``host_only``.
+    """
+
+    def __init__(self, n: int, m: int, row_ptr=None, col_idx=None, *, qc=None,
+                 host_only: bool = False):
+        lib = _lib.load()
+        self._lib = lib
+        self._h = c_vp(None)
+        self._keep = []
+        if qc is not None:
+            base, z = qc
+            base = np.ascontiguousarray(base, dtype=np.int16)
+            desc = QcDesc(base.shape[0], base.shape[1], int(z),
+                          base.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)))
+            self._keep.append(base)
+            st = lib.ldpc_code_create(int(n), int(m), None, None, ctypes.byref(desc),
+                                      1 if host_only else 0, ctypes.byref(self._h))
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+            st = lib.ldpc_code_create(int(n), int(m), c_vp(rp.ctypes.data), c_vp(ci.ctypes.data),
+                                      None, 1 if host_only else 0, ctypes.byref(self._h))
+        _lib.check(st, "ldpc_code_create")
+        n_, m_, k_, r_ = c_i32(), c_i32(), c_i32(), c_i32()
+        nnz = c_i64()
+        _lib.check(lib.ldpc_code_info(self._h, ctypes.byref(n_), ctypes.byref(m_), ctypes.byref(k_),
+                                      ctypes.byref(r_), ctypes.byref(nnz)), "ldpc_code_info")
+        self.n, self.m, self.k, self.rank, self.nnz = n_.value, m_.value, k_.value, r_.value, nnz.value
+        self.host_only = host_only
+        self.device = None if host_only else torch.cuda.current_device()
+
+    @classmethod
+    def from_csr_code(cls, code, host_only: bool = False) -> "Code":
+        """From any object with n, m, row_ptr, col_idx attributes."""
+        return cls(code.n, code.m, code.row_ptr, code.col_idx, host_only=host_only)
+
+    @classmethod
+    def from_qc(cls, base, z: int, host_only: bool = False) -> "Code":
+        base = np.asarray(base)
+        return cls(base.shape[1] * z, base.shape[0] * z, qc=(base, z), host_only=host_only)
+
+    @property
+    def handle(self) -> c_vp:
+        if not self._h:
+            raise ValueError("code is closed")
+        return self._h
+
+    @property
+    def KW(self) -> int:
+        return (self.k + 31) // 32
+
+    @property
+    def NW(self) -> int:
+        return (self.n + 31) // 32
+
+    def positions(self) -> tuple[np.ndarray, np.ndarray]:
+        info = np.zeros(max(self.k, 1), dtype=np.int32)
+        par = np.zeros(max(self.rank, 1), dtype=np.int32)
+        _lib.check(self._lib.ldpc_code_positions(self.handle, c_vp(info.ctypes.data),
+                                                 c_vp(par.ctypes.data)), "ldpc_code_positions")
+        return info[:self.k], par[:self.rank]
+
+    def parity_map(self) -> np.ndarray:
+        """A = P^T as uint32 [rank, KW]."""
+        a = np.zeros((max(self.rank, 1), self.KW), dtype=np.uint32)
+        _lib.check(self._lib.ldpc_code_parity_map(self.handle, c_vp(a.ctypes.data)), "ldpc_code_parity_map")
+        return a[:self.rank]
+
+    def close(self) -> None:
+        if self._h:
+            self._lib.ldpc_code_destroy(self._h)
+            self._h = c_vp(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_dev(t: torch.Tensor, name: str, dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def encode(code: Code, info_words: torch.Tensor, out: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """Systematic encoding (Eq. 3): int32 [F, KW] packed info -> int32 [F, NW] codewords."""
+    F = info_words.shape[0]
+    _check_dev(info_words, "info_words", torch.int32, (F, code.KW))
+    if out is None:
+        out = torch.empty((F, code.NW), dtype=torch.int32, device=info_words.device)
+    _check_dev(out, "out", torch.int32, (F, code.NW))
+    _lib.check(code._lib.ldpc_encode(code.handle, _ptr(info_words), _ptr(out), F,
+                                     _stream_handle(stream)), "ldpc_encode")
+    return out
+
+
+def syndrome(code: Code, bits: torch.Tensor, want_syn: bool = True, stream=None):
+    """H z^T (Eq. 1) of packed words [F, NW] -> (int32 [F, ceil(m/32)] or None, uint8 [F])."""
+    F = bits.shape[0]
+    _check_dev(bits, "bits", torch.int32, (F, code.NW))
+    syn = torch.empty((F, (code.m + 31) // 32), dtype=torch.int32, device=bits.device) if want_syn else None
+    ok = torch.empty((F,), dtype=torch.uint8, device=bits.device)
+    _lib.check(code._lib.ldpc_syndrome(code.handle, _ptr(bits), F, _ptr(syn), _ptr(ok),
+                                       _stream_handle(stream)), "ldpc_syndrome")
+    return syn, ok
+
+
+def _opts(max_iters, early_stop, msg_fp16, schedule, clip) -> DecodeOpts:
+    sched = _SCHED[schedule] if isinstance(schedule, str) else int(schedule)
+    return DecodeOpts(int(max_iters), int(bool(early_stop)), int(bool(msg_fp16)), sched, float(clip))
+
+
+def decode_workspace_size(code: Code, F: int, max_iters: int = 20, early_stop: bool = False,
+                          msg_fp16: bool = False, schedule="auto", clip: float = 20.0) -> int:
+    o = _opts(max_iters, early_stop, msg_fp16, schedule, clip)
+    nbytes = ctypes.c_size_t()
+    _lib.check(code._lib.ldpc_decode_workspace_size(code.handle, int(F), ctypes.byref(o),
+                                                    ctypes.byref(nbytes)), "ldpc_decode_workspace_size")
+    return nbytes.value
+
+
+@dataclass
+class DecodeResult:
+    post: torch.Tensor | None  # float32 [F, n]
+    hard: torch.Tensor         # int32 [F, NW]
+    iters: torch.Tensor        # int32 [F]
+    ok: torch.Tensor           # uint8 [F]
+
+
+def _workspace(nbytes: int, device, workspace: torch.Tensor | None) -> torch.Tensor:
+    if workspace is not None and workspace.numel() >= nbytes:
+        ws = workspace
+    else:
+        ws = torch.empty((max(nbytes, 256),), dtype=torch.uint8, device=device)
+    if ws.data_ptr() % 256:
+        raise ValueError("workspace must be 256-byte aligned")
+    return ws
+
+
+def decode(code: Code, llr: torch.Tensor, max_iters: int = 20, early_stop: bool = False,
+           msg_fp16: bool = False, schedule="auto", clip: float = 20.0, want_post: bool = True,
+           workspace: torch.Tensor | None = None, out: DecodeResult | None = None,
+           stream=None) -> DecodeResult:
+    """Sum-product decoding (Eqs. 4-8) of float32 LLRs [F, n] on the GPU."""
+    F = llr.shape[0]
+    _check_dev(llr, "llr", torch.float32, (F, code.n))
+    dev = llr.device
+    o = _opts(max_iters, early_stop, msg_fp16, schedule, clip)
+    nbytes = ctypes.c_size_t()
+    _lib.check(code._lib.ldpc_decode_workspace_size(code.handle, F, ctypes.byref(o),
+                                                    ctypes.byref(nbytes)), "ldpc_decode_workspace_size")
+    ws = _workspace(nbytes.value, dev, workspace)
+    if out is None:
+        out = DecodeResult(
+            post=torch.empty((F, code.n), dtype=torch.float32, device=dev) if want_post else None,
+            hard=torch.empty((F, code.NW), dtype=torch.int32, device=dev),
+            iters=torch.empty((F,), dtype=torch.int32, device=dev),
+            ok=torch.empty((F,), dtype=torch.uint8, device=dev))
+    _lib.check(code._lib.ldpc_decode(code.handle, _ptr(llr), F, ctypes.byref(o), _ptr(out.post),
+                                     _ptr(out.hard), _ptr(out.iters), _ptr(out.ok), _ptr(ws),
+                                     ws.numel(), _stream_handle(stream)), "ldpc_decode")
+    return out

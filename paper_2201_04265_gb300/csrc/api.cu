@@ -1,0 +1,95 @@
+// Entry points of the C ABI that launch work: argument checks and dispatch.
+#include "ldpc_internal.h"
+
+namespace ldpc {
+int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_decode_opts *o,
+                    float *d_post, uint32_t *d_hard, int32_t *d_iters, uint8_t *d_ok, void *d_work,
+                    size_t work_bytes, cudaStream_t s);
+size_t resident_workspace(const ldpc_code *c, int32_t F, const ldpc_decode_opts *o);
+bool resident_fits(const ldpc_code *c, const ldpc_decode_opts *o);
+
+namespace {
+
+int check_code(const ldpc_code *c) {
+    if (!c) return fail(LDPC_EINVAL, "code is NULL");
+    if (!c->on_device) return fail(LDPC_EINVAL, "code was created host-only");
+    int dev = -1;
+    LDPC_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev != c->device)
+        return fail(LDPC_EINVAL, "code lives on device %d but device %d is current", c->device, dev);
+    return LDPC_OK;
+}
+
+int check_opts(const ldpc_decode_opts *o) {
+    if (!o) return fail(LDPC_EINVAL, "opts is NULL");
+    if (o->max_iters < 0) return fail(LDPC_EINVAL, "max_iters < 0");
+    if (!(o->clip > 0.f) || o->clip > 1e30f) return fail(LDPC_EINVAL, "clip must be positive and finite");
+    if (o->early_stop != 0 && o->early_stop != 1) return fail(LDPC_EINVAL, "early_stop must be 0 or 1");
+    if (o->msg_fp16 != 0 && o->msg_fp16 != 1) return fail(LDPC_EINVAL, "msg_fp16 must be 0 or 1");
+    if (o->schedule < LDPC_SCHED_AUTO || o->schedule > LDPC_SCHED_RESIDENT)
+        return fail(LDPC_EINVAL, "unknown schedule %d", o->schedule);
+    return LDPC_OK;
+}
+
+int pick_schedule(const ldpc_code *c, const ldpc_decode_opts *o) {
+    if (o->schedule != LDPC_SCHED_AUTO) return o->schedule;
+    return resident_fits(c, o) ? LDPC_SCHED_RESIDENT : LDPC_SCHED_PLAIN;
+}
+
+}  // namespace
+}  // namespace ldpc
+
+using namespace ldpc;
+
+extern "C" {
+
+int ldpc_encode(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, int32_t F,
+                ldpc_stream_t stream) {
+    LDPC_TRY(check_code(c));
+    if (F < 0) return fail(LDPC_EINVAL, "F < 0");
+    if (F == 0) return LDPC_OK;
+    if (!d_info || !d_code) return fail(LDPC_EINVAL, "d_info/d_code is NULL");
+    return launch_encode(c, d_info, d_code, F, (cudaStream_t)stream);
+}
+
+int ldpc_syndrome(const ldpc_code *c, const uint32_t *d_bits, int32_t F, uint32_t *d_syn,
+                  uint8_t *d_ok, ldpc_stream_t stream) {
+    LDPC_TRY(check_code(c));
+    if (F < 0) return fail(LDPC_EINVAL, "F < 0");
+    if (F == 0 || (!d_syn && !d_ok)) return LDPC_OK;
+    if (!d_bits) return fail(LDPC_EINVAL, "d_bits is NULL");
+    return launch_syndrome(c, d_bits, F, d_syn, d_ok, (cudaStream_t)stream);
+}
+
+int ldpc_decode_workspace_size(const ldpc_code *c, int32_t F, const ldpc_decode_opts *o,
+                               size_t *bytes) {
+    if (!c || !bytes) return fail(LDPC_EINVAL, "code or bytes is NULL");
+    LDPC_TRY(check_opts(o));
+    if (F < 0) return fail(LDPC_EINVAL, "F < 0");
+    const int sched = pick_schedule(c, o);
+    *bytes = sched == LDPC_SCHED_RESIDENT ? resident_workspace(c, F, o) : plain_workspace(c, F, o);
+    return LDPC_OK;
+}
+
+int ldpc_decode(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_decode_opts *o,
+                float *d_post, uint32_t *d_hard, int32_t *d_iters, uint8_t *d_ok, void *d_work,
+                size_t work_bytes, ldpc_stream_t stream) {
+    LDPC_TRY(check_code(c));
+    LDPC_TRY(check_opts(o));
+    if (F < 0) return fail(LDPC_EINVAL, "F < 0");
+    if (F == 0) return LDPC_OK;
+    if (!d_llr) return fail(LDPC_EINVAL, "d_llr is NULL");
+    if (d_work && (reinterpret_cast<uintptr_t>(d_work) & 255u))
+        return fail(LDPC_EINVAL, "d_work must be 256-byte aligned");
+    const int sched = pick_schedule(c, o);
+    if (sched == LDPC_SCHED_RESIDENT) {
+        if (!resident_fits(c, o))
+            return fail(LDPC_ENOTSUP, "this code does not fit the resident decoder");
+        return decode_resident(c, d_llr, F, o, d_post, d_hard, d_iters, d_ok, d_work, work_bytes,
+                               (cudaStream_t)stream);
+    }
+    return decode_plain(c, d_llr, F, o, d_post, d_hard, d_iters, d_ok, d_work, work_bytes,
+                        (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal declarations shared by the translation units of libldpc.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ldpc.h"
+
+namespace ldpc {
+
+// Sets the calling thread's error message and returns `status`.
+int fail(int status, const char *fmt, ...);
+// Converts a CUDA error into LDPC_ECUDA with a message naming `what`.
+int cuda_fail(cudaError_t err, const char *what);
+
+#define LDPC_TRY_CUDA(expr)                                      \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) return ::ldpc::cuda_fail(_e, #expr); \
+    } while (0)
+
+#define LDPC_TRY(expr)              \
+    do {                            \
+        int _s = (expr);            \
+        if (_s != LDPC_OK) return _s; \
+    } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+// The message clip in the kernels' log2 units.
+inline float clip_log2(float clip) { return (float)((double)clip * 1.4426950408889634); }
+
+// Device-side tables of a code (all owned by the code object).
+struct DeviceCode {
+    int32_t *row_ptr = nullptr;    // [m+1]
+    int32_t *col_idx = nullptr;    // [E]  check-major edge -> bit
+    int32_t *col_ptr = nullptr;    // [n+1]
+    int32_t *col_edge = nullptr;   // [E]  bit-major list of edge ids (ascending)
+    int32_t *info_pos = nullptr;   // [k]
+    int32_t *parity_pos = nullptr; // [rank]
+    uint32_t *AT = nullptr;        // [KW][rank] parity map, word-major
+    // resident decoder tables (see decode_resident.cu)
+    uint32_t *res_edges = nullptr; // per check-slot packed (bit index, slot) records
+    int32_t res_edges_len = 0;
+};
+
+// Resident-decoder plan: how one frame's checks and bits are laid out in
+// shared memory (built on the host at create time).
+struct ResidentPlan {
+    bool ok = false;          // the code has a resident layout
+    bool pad_slots = false;   // some bits have fewer than dv_pad edges
+    int32_t dc_pad = 0;       // row degree padded to an instantiated shape
+    int32_t dv_pad = 0;       // slots per bit in the bit-major message array
+    int32_t rows_pad = 0;     // threads per CTA of the resident launch
+    std::vector<uint32_t> edges; // [cpt * ceil(dc_pad/2)][threads] 16-bit slot pairs
+};
+
+}  // namespace ldpc
+
+struct ldpc_code {
+    int32_t n = 0, m = 0, k = 0, rank = 0;
+    int64_t nnz = 0;
+    int32_t KW = 0, NW = 0, MW = 0;  // words per info word, codeword, syndrome
+    int32_t dc_max = 0, dv_max = 0, dc_min = 0, dv_min = 0;
+    std::vector<int32_t> row_ptr, col_idx, col_ptr, col_edge, info_pos, parity_pos;
+    std::vector<uint32_t> A;  // [rank][KW]
+    bool on_device = false;
+    int device = -1;
+    ldpc::DeviceCode d;
+    ldpc::ResidentPlan res;
+};
+
+namespace ldpc {
+// Kernel launchers (defined in the .cu files).
+int launch_encode(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, int32_t F,
+                  cudaStream_t s);
+int launch_syndrome(const ldpc_code *c, const uint32_t *d_bits, int32_t F, uint32_t *d_syn,
+                    uint8_t *d_ok, cudaStream_t s);
+size_t plain_workspace(const ldpc_code *c, int32_t F, const ldpc_decode_opts *o);
+int decode_plain(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_decode_opts *o,
+                 float *d_post, uint32_t *d_hard, int32_t *d_iters, uint8_t *d_ok, void *d_work,
+                 size_t work_bytes, cudaStream_t s);
+}  // namespace ldpc
