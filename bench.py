@@ -1,0 +1,433 @@
+"""Benchmark: decoded information Gbit/s of LDPC sum-product decoding on GB300.
+
+Workload (the large plain-method configuration): a random (3,6)-regular code
+with n = 8064 (rate 1/2), batches of F = 65536 frames, BPSK over AWGN at
+Eb/N0 in {1.5, 2.0, 2.5} dB (steps cycle through the three), 50 fixed
+iterations.  One step is one pass of the hot path over one batch: systematic
+encoding of the batch's information words (K1) and decoding of its channel
+LLRs (K5, the persistent shared-memory decoder with binary16 message storage
+and FP32 arithmetic).  The plain FP32 decoder with messages in HBM (K3/K4) is
+timed on the same inputs for comparison, with frame-error counts of both.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank decodes its own batch (frames are independent; no
+collective on the data path) and rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BITS, DV, DC, CODE_SEED = 8064, 3, 6, 2
+FRAMES = 65536
+EBN0 = (1.5, 2.0, 2.5)
+ITERS = 50
+METRIC = "decoded info Gbit/s at fixed iterations, batched/FP16 vs plain FP32 on one GB300"
+WORKLOAD = "random (3,6)-regular LDPC n=8064 rate 1/2, 65536 frames/batch, BPSK-AWGN Eb/N0 1.5/2.0/2.5 dB, 50 fixed iterations"
+MUFU_PER_EDGE_ITER = 3           # ex2, rcp, lg2 per edge and iteration (check update)
+MUFU_PER_CLK_SM = 16             # XU pipe results per clock per SM
+SMS = 152
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def _make_inputs(L, torch, code, dev, seed):
+    """Seeded synthetic inputs on the device: info words, their codewords
+    (encoded by the library), and channel LLRs for each Eb/N0 point."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    info = torch.randint(0, 2 ** 32, (FRAMES, code.KW), dtype=torch.int64, device=dev,
+                         generator=g).to(torch.int32)
+    if code.k % 32:  # zero the pad bits of the last word
+        info[:, -1] &= (1 << (code.k % 32)) - 1
+    cw_words = L.encode(code, info)
+    shifts = torch.arange(32, device=dev, dtype=torch.int32)
+    bits = ((cw_words.unsqueeze(-1) >> shifts) & 1).reshape(FRAMES, -1)[:, :code.n].to(torch.float32)
+    rate = code.k / code.n
+    llrs = []
+    for ebn0 in EBN0:
+        s2 = 1.0 / (2.0 * rate * 10.0 ** (ebn0 / 10.0))
+        noise = torch.randn((FRAMES, code.n), device=dev, generator=g)
+        y = (2.0 * bits - 1.0) + (s2 ** 0.5) * noise
+        llrs.append((2.0 * y / s2).contiguous())
+        del noise, y
+    return info, cw_words, llrs
+
+
+def _frame_errors(torch, hard, cw_words):
+    return int((hard != cw_words).any(dim=1).sum().item())
+
+
+def run_ours(args):
+    import torch
+    import __graft_entry__
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        if rank == 0:
+            __graft_entry__.build()
+        dist.barrier()
+    else:
+        __graft_entry__.build()
+    import ldpc_synth as S
+    import paper_2201_04265_gb300 as L
+
+    h = S.random_regular(N_BITS, DV, DC, seed=CODE_SEED)
+    code = L.Code.from_csr_code(h)
+    info, cw_words, llrs = _make_inputs(L, torch, code, dev, seed=1000 + rank)
+    stream = torch.cuda.current_stream()
+    opts = dict(max_iters=ITERS, early_stop=False, msg_fp16=True, schedule="resident", want_post=False)
+    ws = torch.empty(L.decode_workspace_size(code, FRAMES, **{k: v for k, v in opts.items() if k != "want_post"}),
+                     dtype=torch.uint8, device=dev)
+    out = L.decode(code, llrs[0], workspace=ws, **opts)
+    cw_out = torch.empty_like(cw_words)
+
+    def step(i):
+        L.encode(code, info, out=cw_out)
+        L.decode(code, llrs[i % len(EBN0)], workspace=ws, out=out, **opts)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        step(i)
+    barrier()
+    peaks, peak_src = _peaks()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # per-kernel timing of the decode kernel inside the timed region
+    dec_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        barrier()
+        start.record(stream)
+        for i in range(args.steps):
+            L.encode(code, info, out=cw_out)
+            dec_ev[i][0].record(stream)
+            L.decode(code, llrs[i % len(EBN0)], workspace=ws, out=out, **opts)
+            dec_ev[i][1].record(stream)
+        end.record(stream)
+        barrier()
+    t_ms = start.elapsed_time(end)
+    dec_ms = [a.elapsed_time(b) for a, b in dec_ev]
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    bits_per_step = FRAMES * code.k
+    value = world * bits_per_step / (ms_per_step * 1e-3) / 1e9
+
+    # --- frame errors: FP16 resident vs plain FP32 on identical inputs
+    fer = {}
+    plain_opts = dict(max_iters=ITERS, early_stop=False, msg_fp16=False, schedule="plain", want_post=False)
+    ws_plain = torch.empty(L.decode_workspace_size(code, FRAMES, **{k: v for k, v in plain_opts.items()
+                                                                      if k != "want_post"}),
+                           dtype=torch.uint8, device=dev)
+    plain_ms = []
+    for j, ebn0 in enumerate(EBN0):
+        r16 = L.decode(code, llrs[j], workspace=ws, **opts)
+        fe16 = _frame_errors(torch, r16.hard, cw_words)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r32 = L.decode(code, llrs[j], workspace=ws_plain, **plain_opts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(a.elapsed_time(b))
+        fe32 = _frame_errors(torch, r32.hard, cw_words)
+        fer[f"{ebn0}dB"] = {"fp16_resident": fe16 / FRAMES, "fp32_plain": fe32 / FRAMES,
+                            "equal_within_0.1pct": abs(fe16 - fe32) <= 0.001 * FRAMES}
+        del r32
+    del ws_plain
+    plain_gbps = bits_per_step / (statistics.median(plain_ms) * 1e-3) / 1e9
+
+    # --- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_llr = [x.cpu().pin_memory() for x in llrs]
+        host_info = info.cpu().pin_memory()
+        host_hard = torch.empty(out.hard.shape, dtype=torch.int32).pin_memory()
+        host_ok = torch.empty(out.ok.shape, dtype=torch.uint8).pin_memory()
+        d_llr = torch.empty_like(llrs[0])
+        d_info = torch.empty_like(info)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(args.e2e_steps):
+            d_info.copy_(host_info, non_blocking=True)
+            d_llr.copy_(host_llr[i % len(EBN0)], non_blocking=True)
+            L.encode(code, d_info, out=cw_out)
+            L.decode(code, d_llr, workspace=ws, out=out, **opts)
+            host_hard.copy_(out.hard, non_blocking=True)
+            host_ok.copy_(out.ok, non_blocking=True)
+        b.record(stream)
+        barrier()
+        e_ms = a.elapsed_time(b) / args.e2e_steps
+        h2d = host_llr[0].numel() * 4 + host_info.numel() * 4
+        d2h = host_hard.numel() * 4 + host_ok.numel()
+        e2e = {"value": round(world * bits_per_step / (e_ms * 1e-3) / 1e9, 4), "unit": "Gbit/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(e_ms, 3), "steps": args.e2e_steps}
+
+    # --- roofline of the dominant kernel (the resident decoder): MUFU-bound
+    dec_avg_s = statistics.mean(dec_ms) * 1e-3
+    edge_iters = FRAMES * code.nnz * ITERS
+    achieved = MUFU_PER_EDGE_ITER * edge_iters / dec_avg_s / 1e12
+    peak_mufu = MUFU_PER_CLK_SM * SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    clk = clocks.summary()
+    traffic = _recorded_traffic()
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_mufu, 4),
+                "unit": "Tops/s (MUFU ex2/rcp/lg2)", "frac": round(achieved / peak_mufu, 4),
+                "traffic": traffic, "kernel": "resident_kernel<half,2,6,8>",
+                "peak_source": f"{MUFU_PER_CLK_SM} XU results/clk/SM x {SMS} SMs x sm_max_mhz ({peak_src})",
+                "decode_ms_avg": round(dec_avg_s * 1e3, 3)}
+    plain_bytes = FRAMES * ITERS * (3 * 4 * code.nnz + 3 * 4 * code.n)
+    plain_roof = {"bound": "hbm", "achieved": round(plain_bytes / (statistics.median(plain_ms) * 1e-3) / 1e9, 1),
+                  "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                  "frac": round(plain_bytes / (statistics.median(plain_ms) * 1e-3) / 1e9 / peaks.get("hbm_gbs"), 4),
+                  "note": f"algorithmic bytes, {peak_src} peak"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(h, seconds=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "Gbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (fp16 messages)",
+            "data": "synthetic (seeded info bits, library-encoded codewords, BPSK-AWGN LLRs)",
+            "config": {"workload": WORKLOAD, "n": code.n, "k": code.k, "edges": code.nnz,
+                       "frames_per_step": FRAMES, "iterations": ITERS, "early_stop": False,
+                       "decoder": "resident (shared-memory), fp16 message storage",
+                       "step": "encode batch (K1) + decode batch (K5)",
+                       "l2": "inputs larger than L2 (2.1 GB LLRs per batch)", "parallelism": f"replicas x{world}"},
+            "plain_fp32": {"value": round(plain_gbps, 4), "unit": "Gbit/s", "ms": round(statistics.median(plain_ms), 3),
+                           "roofline": plain_roof},
+            "speedup_vs_plain_fp32": round(value / world / plain_gbps, 3),
+            "fer": fer,
+            "roofline": roofline,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _recorded_traffic():
+    """DRAM bytes per launch of the resident kernel from the committed ncu
+    summary (None when no capture of the current kernel is recorded)."""
+    path = os.path.join(ROOT, "profiles", "resident_traffic.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh).get("bytes_per_launch")
+    return None
+
+
+# ------------------------------------------------------- CPU oracle baseline
+
+
+def cpu_baseline(h, seconds: float = 15.0, ebn0: float = 2.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import ldpc_synth as S
+    import oracle
+    nthreads = os.cpu_count() or 1
+    sysm = oracle.systematic(h)
+    rate = sysm.k / h.n
+
+    def sample(F, seed):
+        msgs = S.info_bits(F, sysm.k, seed)
+        cw = oracle.encode(sysm, msgs)
+        return S.bpsk_awgn_llr(cw, ebn0, rate, S.frame_noise(F, h.n, seed + 1))
+
+    calib = sample(nthreads, 7)
+    t0 = time.perf_counter()
+    oracle.decode(h, calib, iters=ITERS, nthreads=nthreads)
+    per_round = time.perf_counter() - t0
+    rounds = max(1, int(seconds / max(per_round, 1e-3)))
+    F = nthreads * rounds
+    llr = sample(F, 9)
+    t0 = time.perf_counter()
+    oracle.decode(h, llr, iters=ITERS, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return {"value": round(F * sysm.k / dt / 1e9, 6), "unit": "Gbit/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"{F} frames of the same code at Eb/N0 {ebn0} dB, {ITERS} iterations, FP64, "
+                      f"{nthreads} threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores, each step a
+    bounded sample of the workload.  Under torchrun only rank 0 runs."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import ldpc_synth as S
+    import oracle
+    h = S.random_regular(N_BITS, DV, DC, seed=CODE_SEED)
+    sysm = oracle.systematic(h)
+    nthreads = os.cpu_count() or 1
+    F = nthreads * args.ref_frames_per_thread
+    rate = sysm.k / h.n
+    msgs = S.info_bits(F, sysm.k, 31)
+    cw = oracle.encode(sysm, msgs)
+    llrs = [S.bpsk_awgn_llr(cw, e, rate, S.frame_noise(F, h.n, 32 + i)) for i, e in enumerate(EBN0)]
+    for i in range(args.warmup):
+        oracle.decode(h, llrs[i % 3][:nthreads], iters=ITERS, nthreads=nthreads)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.decode(h, llrs[i % 3], iters=ITERS, nthreads=nthreads)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = F * sysm.k / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gbit/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": F, "iterations": ITERS,
+                   "note": "bounded sample of the batch per step (FP64 CPU oracle)"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gbit/s", "cores": nthreads, "kind": "oracle",
+                         "sample": f"{F} frames per step"},
+        "e2e": {"value": round(value, 6), "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_profile_case(args):
+    """One decode of a small batch of the same code, for single-kernel ncu
+    captures (inputs still larger than L2, a few hundred MB on the device)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import ldpc_synth as S
+    import paper_2201_04265_gb300 as L
+    torch.cuda.set_device(0)
+    code = L.Code.from_csr_code(S.random_regular(N_BITS, DV, DC, seed=CODE_SEED))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    llr = (torch.randn((args.frames, code.n), device="cuda", generator=g) * 3.0 + 2.5).contiguous()
+    if args.profile_case == "resident":
+        r = L.decode(code, llr, max_iters=ITERS, schedule="resident", msg_fp16=True, want_post=False)
+    else:
+        r = L.decode(code, llr, max_iters=3, schedule="plain", msg_fp16=False, want_post=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "frames": args.frames, "ok_frames": int(r.ok.sum())}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=12)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-frames-per-thread", type=int, default=4)
+    ap.add_argument("--profile-case", choices=["resident", "plain"], default=None,
+                    help="run one small decode (for ncu captures) instead of the benchmark")
+    ap.add_argument("--frames", type=int, default=4096, help="frames of the --profile-case run")
+    args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

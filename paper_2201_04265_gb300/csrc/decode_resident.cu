@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kResVPT = 16;       // bits per thread
 constexpr int kResMaxThreads = 512;
-constexpr int kResDV = 3;         // padded column degree (slots per bit)
+constexpr int kResSlots = 4;      // message slots per bit (column degree <= 4)
 constexpr uint32_t kNoSlot = 0xFFFFu;
 
 // Row shapes: padded row degree and checks per thread (about 48 edges/thread).
@@ -61,30 +61,38 @@ struct LVec<2> {
     __device__ static T make(const float *x) { return make_float2(x[0], x[1]); }
 };
 
+// One message slot holding G frames, and the 16-byte record of a bit's slots.
 template <class MsgT, int G>
 struct EVec;
 template <>
 struct EVec<__half, 2> {
     using T = __half2;
+    using Rec = uint4;  // 4 x half2
     __device__ static void get(T v, float *x) {
         const float2 f = __half22float2(v);
         x[0] = f.x;
         x[1] = f.y;
     }
     __device__ static T make(const float *x) { return __floats2half2_rn(x[0], x[1]); }
-    __device__ static T zero() { return __floats2half2_rn(0.f, 0.f); }
+    __device__ static void slot(const Rec &r, int q, float *x) {
+        const uint32_t w = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+        get(*reinterpret_cast<const __half2 *>(&w), x);
+    }
 };
 template <>
 struct EVec<float, 1> {
     using T = float;
+    using Rec = float4;
     __device__ static void get(T v, float *x) { x[0] = v; }
     __device__ static T make(const float *x) { return x[0]; }
-    __device__ static T zero() { return 0.f; }
+    __device__ static void slot(const Rec &r, int q, float *x) {
+        x[0] = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+    }
 };
 
 struct ResArgs {
     const float *llr;
-    int32_t F, n, m, NW, T_iters, early_stop, pad_slots;
+    int32_t F, n, m, NW, T_iters, early_stop;
     float clip2;
     const uint32_t *edges;  // [CPT * DCW][T]
     float *post;
@@ -94,66 +102,82 @@ struct ResArgs {
     unsigned *counter;
 };
 
-// One check pass over the thread's checks.  COMPUTE = false evaluates only the
-// syndrome.  Returns bit i set when a check of frame i is unsatisfied by the
-// hard decisions z = [L >= 0] read in this pass.
-template <class MsgT, int G, int DC, int CPT, bool COMPUTE>
+// Shared-memory layout of a group: Ls[n] (LV::T) then Es[n][4] (EV::T), so
+// that the 16-bit slot s = 4 v + r of an edge gives both addresses:
+// message at byte 4 s * sizeof(slot) / 4, total LLR of bit v = s >> 2.
+template <class MsgT, int G>
+struct Smem {
+    unsigned char *L;  // Ls base
+    unsigned char *E;  // Es base
+    __device__ typename LVec<G>::T &Lv(uint32_t s) const {
+        return *reinterpret_cast<typename LVec<G>::T *>(L + (s >> 2) * sizeof(typename LVec<G>::T));
+    }
+    __device__ typename EVec<MsgT, G>::T &Ev(uint32_t s) const {
+        return *reinterpret_cast<typename EVec<MsgT, G>::T *>(E + s * sizeof(typename EVec<MsgT, G>::T));
+    }
+};
+
+__device__ __forceinline__ uint32_t slot_of(const uint32_t *w, int j) {
+    return (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xFFFFu);
+}
+
+// Check pass over the thread's checks, rows of exactly DC edges (REG) or of
+// at most DC edges with unused slots marked kNoSlot.  Updates the messages in
+// place.  With SYN, also returns bit i set when frame i has a check that the
+// hard decisions z = [L >= 0] (L as left by the last bit pass) do not satisfy.
+template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN>
 __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                               typename LVec<G>::T *Ls,
-                                               typename EVec<MsgT, G>::T *Es, bool first,
-                                               float clip2) {
+                                               const Smem<MsgT, G> &sm, float clip2) {
     using LV = LVec<G>;
     using EV = EVec<MsgT, G>;
-    uint32_t bad = 0;
+    uint32_t zacc[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) zacc[i] = 0;
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
         if ((idx[k][0] & 0xFFFFu) == kNoSlot) continue;  // no check in this slot
         uint32_t slot[DC];
 #pragma unroll
-        for (int j = 0; j < DC; ++j) slot[j] = (idx[k][j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+        for (int j = 0; j < DC; ++j) slot[j] = slot_of(idx[k], j);
         float u[DC][G];
-        uint32_t smask[G], zpar[G];
+        uint32_t xbits[DC][G], sacc[G], zsgn[G];
         int d = 0;
 #pragma unroll
-        for (int i = 0; i < G; ++i) smask[i] = zpar[i] = 0;
+        for (int i = 0; i < G; ++i) sacc[i] = zsgn[i] = 0;
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
-            if (slot[j] != kNoSlot) {
+            if (REG || slot[j] != kNoSlot) {
                 ++d;
                 float L[G], Eo[G];
-                LV::get(Ls[slot[j] / kResDV], L);
-                if (COMPUTE) {
-                    if (first) {
-#pragma unroll
-                        for (int i = 0; i < G; ++i) Eo[i] = 0.f;
-                    } else {
-                        EV::get(Es[slot[j]], Eo);
-                    }
-                }
+                LV::get(sm.Lv(slot[j]), L);
+                EV::get(sm.Ev(slot[j]), Eo);
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
-                    zpar[i] ^= (uint32_t)(L[i] >= 0.f);
-                    if (COMPUTE) {
-                        const float x = check_input(L[i], Eo[i], clip2);
-                        smask[i] |= (__float_as_uint(x) >> 31) << j;
-                        u[j][i] = check_u(x);
-                    }
+                    if (SYN) zsgn[i] ^= __float_as_uint(L[i]);  // bit 31: parity of [L < 0]
+                    const float x = L[i] - Eo[i];  // Eq. 6 rearranged
+                    xbits[j][i] = __float_as_uint(x);
+                    sacc[i] ^= xbits[j][i];
+                    u[j][i] = ex2_approx(-fminf(fabsf(x), clip2));
                 }
             } else {
 #pragma unroll
-                for (int i = 0; i < G; ++i) u[j][i] = 0.f;  // identity for the pair products
+                for (int i = 0; i < G; ++i) {
+                    u[j][i] = 0.f;  // identity for the pair products
+                    xbits[j][i] = 0u;
+                }
             }
         }
+        // parity of z = [L >= 0] over the row = d + parity of [L < 0] (the bit
+        // pass leaves no -0, so the sign bit is exactly [L < 0])
+        if (SYN)
 #pragma unroll
-        for (int i = 0; i < G; ++i) bad |= zpar[i] << i;
-        if (!COMPUTE) continue;
+            for (int i = 0; i < G; ++i) zacc[i] |= (zsgn[i] >> 31) ^ (uint32_t)(d & 1);
+        // (-1)^d folded into the accumulated sign bit
+#pragma unroll
+        for (int i = 0; i < G; ++i) sacc[i] ^= (uint32_t)(d & 1) << 31;
         EvOd pre[DC][G];
-        uint32_t sall[G];
 #pragma unroll
-        for (int i = 0; i < G; ++i) {
-            pre[0][i] = {1.f, 0.f};
-            sall[i] = (__popc(smask[i]) + d) & 1u;
-        }
+        for (int i = 0; i < G; ++i) pre[0][i] = {1.f, 0.f};
 #pragma unroll
         for (int j = 1; j < DC; ++j)
 #pragma unroll
@@ -163,32 +187,99 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
         for (int i = 0; i < G; ++i) suf[i] = {1.f, 0.f};
 #pragma unroll
         for (int j = DC - 1; j >= 0; --j) {
-            if (slot[j] != kNoSlot) {
+            if (REG || slot[j] != kNoSlot) {
                 float out[G];
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
                     const float mag = evod_magnitude(evod_join(pre[j][i], suf[i]), clip2);
-                    const uint32_t sgn = sall[i] ^ ((smask[i] >> j) & 1u);
-                    out[i] = sgn ? -mag : mag;
+                    out[i] = __uint_as_float(__float_as_uint(mag) |
+                                             ((sacc[i] ^ xbits[j][i]) & 0x80000000u));
                     suf[i] = evod_add(suf[i], u[j][i]);
                 }
-                Es[slot[j]] = EV::make(out);
+                sm.Ev(slot[j]) = EV::make(out);
             }
         }
+    }
+    uint32_t bad = 0;
+    if (SYN)
+#pragma unroll
+        for (int i = 0; i < G; ++i) bad |= (zacc[i] & 1u) << i;
+    return bad;
+}
+
+// Syndrome of z = [L >= 0] over the thread's checks (no message update).
+template <class MsgT, int G, int DC, int CPT>
+__device__ __forceinline__ uint32_t syndrome_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
+                                                  const Smem<MsgT, G> &sm) {
+    uint32_t bad = 0;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        uint32_t par = 0;
+#pragma unroll
+        for (int j = 0; j < DC; ++j) {
+            const uint32_t s = slot_of(idx[k], j);
+            if (s == kNoSlot) continue;
+            float L[G];
+            LVec<G>::get(sm.Lv(s), L);
+#pragma unroll
+            for (int i = 0; i < G; ++i) par ^= (uint32_t)(L[i] >= 0.f) << i;
+        }
+        bad |= par;  // a check with odd parity is unsatisfied
     }
     return bad;
 }
 
-template <class MsgT, int G, int DC, int CPT>
+// Bit pass (Eq. 7): L_v = R_v + the bit's message slots in ascending edge
+// order; frames not in `active` keep their L_v.  REG codes have exactly three
+// edges per bit; otherwise all four slots are summed (unused ones hold 0).
+template <class MsgT, int G, bool REG, bool SYN>
+__device__ __forceinline__ void bit_pass(const float (&R)[kResVPT][G], const Smem<MsgT, G> &sm,
+                                         int n, int T, uint32_t active, uint32_t exists) {
+    using LV = LVec<G>;
+    using EV = EVec<MsgT, G>;
+    constexpr int NS = REG ? 3 : kResSlots;
+#pragma unroll
+    for (int k = 0; k < kResVPT; ++k) {
+        const int v = threadIdx.x + k * T;
+        if (v < n) {
+            const typename EV::Rec rec =
+                *reinterpret_cast<const typename EV::Rec *>(sm.E + (size_t)v * kResSlots * sizeof(typename EV::T));
+            float L[G];
+#pragma unroll
+            for (int i = 0; i < G; ++i) L[i] = R[k][i];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                float e[G];
+                EV::slot(rec, q, e);
+#pragma unroll
+                for (int i = 0; i < G; ++i) L[i] += e[i];
+            }
+            if (SYN)
+#pragma unroll
+                for (int i = 0; i < G; ++i) L[i] += 0.f;  // no -0: z = [L >= 0] by sign
+            typename LV::T *dst = reinterpret_cast<typename LV::T *>(sm.L) + v;
+            if (active != exists) {
+                float old[G];
+                LV::get(*dst, old);
+#pragma unroll
+                for (int i = 0; i < G; ++i)
+                    if (!((active >> i) & 1u)) L[i] = old[i];
+            }
+            *dst = LV::make(L);
+        }
+    }
+}
+
+template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN>
 __global__ void __launch_bounds__(kResMaxThreads)
 resident_kernel(ResArgs a) {
     using LV = LVec<G>;
     using EV = EVec<MsgT, G>;
     constexpr int DCW = (DC + 1) / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename LV::T *Ls = reinterpret_cast<typename LV::T *>(smem_raw);
-    const size_t lbytes = ((size_t)a.n * sizeof(typename LV::T) + 15) & ~size_t(15);
-    typename EV::T *Es = reinterpret_cast<typename EV::T *>(smem_raw + lbytes);
+    Smem<MsgT, G> sm;
+    sm.L = smem_raw;
+    sm.E = smem_raw + (((size_t)a.n * sizeof(typename LV::T) + 15) & ~size_t(15));
     __shared__ int s_group;
 
     const int T = blockDim.x, tid = threadIdx.x;
@@ -211,7 +302,7 @@ resident_kernel(ResArgs a) {
 #pragma unroll
         for (int i = 0; i < G; ++i) exists |= (uint32_t)(f0 + i < a.F) << i;
 
-        // channel LLRs (log2 units) into registers and L_v = R_v into Ls
+        // channel LLRs (log2 units) into registers and L_v = R_v; messages 0
         float R[kResVPT][G];
 #pragma unroll
         for (int k = 0; k < kResVPT; ++k) {
@@ -219,10 +310,14 @@ resident_kernel(ResArgs a) {
 #pragma unroll
             for (int i = 0; i < G; ++i)
                 R[k][i] = (v < a.n && ((exists >> i) & 1u)) ? a.llr[(f0 + i) * a.n + v] * kLog2e : 0.f;
-            if (v < a.n) Ls[v] = LV::make(R[k]);
+            if (v < a.n) {
+                reinterpret_cast<typename LV::T *>(sm.L)[v] = LV::make(R[k]);
+                *reinterpret_cast<uint4 *>(sm.E + (size_t)v * kResSlots * sizeof(typename EV::T)) =
+                    make_uint4(0u, 0u, 0u, 0u);
+                if (sizeof(typename EV::T) == 8)
+                    *reinterpret_cast<uint4 *>(sm.E + (size_t)v * kResSlots * 8 + 16) = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
-        if (a.pad_slots)
-            for (int s = tid; s < a.n * kResDV; s += T) Es[s] = EV::zero();
         __syncthreads();
 
         uint32_t active = exists, okm = 0;
@@ -230,8 +325,8 @@ resident_kernel(ResArgs a) {
 #pragma unroll
         for (int i = 0; i < G; ++i) it_done[i] = 0;
         for (int t = 1; t <= a.T_iters; ++t) {
-            const uint32_t bad = check_pass<MsgT, G, DC, CPT, true>(idx, Ls, Es, t == 1, a.clip2);
-            if (a.early_stop && t >= 2) {
+            if (SYN && t >= 2) {
+                const uint32_t bad = check_pass<MsgT, G, DC, CPT, REG, true>(idx, sm, a.clip2);
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
                     const int any_bad = __syncthreads_or((int)((bad >> i) & 1u));
@@ -243,37 +338,14 @@ resident_kernel(ResArgs a) {
                 }
                 if (!active) break;
             } else {
+                check_pass<MsgT, G, DC, CPT, REG, false>(idx, sm, a.clip2);
                 __syncthreads();
             }
-            // bit pass (Eq. 7), frozen frames keep their L_v
-#pragma unroll
-            for (int k = 0; k < kResVPT; ++k) {
-                const int v = tid + k * T;
-                if (v < a.n) {
-                    float L[G];
-#pragma unroll
-                    for (int i = 0; i < G; ++i) L[i] = R[k][i];
-#pragma unroll
-                    for (int q = 0; q < kResDV; ++q) {
-                        float e[G];
-                        EV::get(Es[v * kResDV + q], e);
-#pragma unroll
-                        for (int i = 0; i < G; ++i) L[i] += e[i];
-                    }
-                    if (active != exists) {
-                        float old[G];
-                        LV::get(Ls[v], old);
-#pragma unroll
-                        for (int i = 0; i < G; ++i)
-                            if (!((active >> i) & 1u)) L[i] = old[i];
-                    }
-                    Ls[v] = LV::make(L);
-                }
-            }
+            bit_pass<MsgT, G, REG, SYN>(R, sm, a.n, T, active, exists);
             __syncthreads();
         }
         if (active) {  // frames that ran every iteration: syndrome of the final z
-            const uint32_t bad = check_pass<MsgT, G, DC, CPT, false>(idx, Ls, Es, false, a.clip2);
+            const uint32_t bad = syndrome_pass<MsgT, G, DC, CPT>(idx, sm);
 #pragma unroll
             for (int i = 0; i < G; ++i) {
                 const int any_bad = __syncthreads_or((int)((bad >> i) & 1u));
@@ -290,7 +362,7 @@ resident_kernel(ResArgs a) {
             const int v0 = v - lane;
             float L[G];
             if (v < a.n) {
-                LV::get(Ls[v], L);
+                LV::get(reinterpret_cast<typename LV::T *>(sm.L)[v], L);
             } else {
 #pragma unroll
                 for (int i = 0; i < G; ++i) L[i] = 0.f;
@@ -319,13 +391,19 @@ resident_kernel(ResArgs a) {
 
 using KernelFn = void (*)(ResArgs);
 
+template <class MsgT, int G, int DC, int CPT>
+KernelFn pick_flags(bool reg, bool syn) {
+    if (reg) return syn ? resident_kernel<MsgT, G, DC, CPT, true, true> : resident_kernel<MsgT, G, DC, CPT, true, false>;
+    return syn ? resident_kernel<MsgT, G, DC, CPT, false, true> : resident_kernel<MsgT, G, DC, CPT, false, false>;
+}
+
 template <class MsgT, int G>
-KernelFn pick_kernel(int dc) {
+KernelFn pick_kernel(int dc, bool reg, bool syn) {
     switch (dc) {
-        case 6: return resident_kernel<MsgT, G, 6, 8>;
-        case 9: return resident_kernel<MsgT, G, 9, 5>;
-        case 12: return resident_kernel<MsgT, G, 12, 4>;
-        case 16: return resident_kernel<MsgT, G, 16, 3>;
+        case 6: return pick_flags<MsgT, G, 6, 8>(reg, syn);
+        case 9: return pick_flags<MsgT, G, 9, 5>(reg, syn);
+        case 12: return pick_flags<MsgT, G, 12, 4>(reg, syn);
+        case 16: return pick_flags<MsgT, G, 16, 3>(reg, syn);
         default: return nullptr;
     }
 }
@@ -333,17 +411,18 @@ KernelFn pick_kernel(int dc) {
 size_t res_smem(const ldpc_code *c, bool fp16) {
     const int G = fp16 ? 2 : 1;
     const size_t lbytes = ((size_t)c->n * 4 * G + 15) & ~size_t(15);
-    return lbytes + (size_t)c->n * kResDV * (fp16 ? 2 : 4) * G;
+    return lbytes + (size_t)c->n * kResSlots * (fp16 ? 2 : 4) * G;
 }
 
 }  // namespace
 
-// Host-side plan: pick the row shape, the thread count, and lay out each
+// Host-side plan: pick the row shape and the thread count, and lay out each
 // thread's edge slots as [CPT * DCW][T] 32-bit words (two 16-bit slots each).
+// The slot of an edge is 4 v + r, v its bit and r its rank in v's column.
 int build_resident_plan(ldpc_code *c) {
     ResidentPlan &p = c->res;
     p = ResidentPlan{};
-    if (c->dv_max > kResDV || (int64_t)c->n * kResDV > 0xFFFE) return LDPC_OK;
+    if (c->dv_max > kResSlots || (int64_t)c->n * kResSlots > 0xFFFE) return LDPC_OK;
     const Shape *shape = nullptr;
     for (const Shape &s : kShapes)
         if (s.dc >= c->dc_max) {
@@ -355,11 +434,10 @@ int build_resident_plan(ldpc_code *c) {
     const int T = (int)ceil_div(need, 32) * 32;
     if (T > kResMaxThreads) return LDPC_OK;
     const int DCW = (shape->dc + 1) / 2;
-    // slot of each edge: bit * DV + rank of the edge within its bit's column
     std::vector<uint32_t> slot_of((size_t)c->nnz);
     for (int32_t v = 0; v < c->n; ++v)
         for (int32_t q = c->col_ptr[v]; q < c->col_ptr[v + 1]; ++q)
-            slot_of[c->col_edge[q]] = (uint32_t)(v * kResDV + (q - c->col_ptr[v]));
+            slot_of[c->col_edge[q]] = (uint32_t)(v * kResSlots + (q - c->col_ptr[v]));
     p.edges.assign((size_t)shape->cpt * DCW * T, 0xFFFFFFFFu);
     for (int t = 0; t < T; ++t)
         for (int k = 0; k < shape->cpt; ++k) {
@@ -373,9 +451,10 @@ int build_resident_plan(ldpc_code *c) {
             }
         }
     p.dc_pad = shape->dc;
-    p.dv_pad = kResDV;
+    p.dv_pad = kResSlots;
     p.rows_pad = T;  // thread count of the launch
-    p.pad_slots = c->dv_min < kResDV;
+    // exactly dc edges per check and three per bit: the specialised kernels
+    p.regular = c->dc_min == shape->dc && c->dc_max == shape->dc && c->dv_min == 3 && c->dv_max == 3;
     p.ok = true;
     return LDPC_OK;
 }
@@ -392,7 +471,9 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
                     size_t work_bytes, cudaStream_t s) {
     if (!d_work || work_bytes < 256) return fail(LDPC_EINVAL, "workspace too small (need 256 bytes)");
     const bool fp16 = o->msg_fp16 != 0;
-    KernelFn fn = fp16 ? pick_kernel<__half, 2>(c->res.dc_pad) : pick_kernel<float, 1>(c->res.dc_pad);
+    const bool syn = o->early_stop != 0 && o->max_iters >= 2;
+    KernelFn fn = fp16 ? pick_kernel<__half, 2>(c->res.dc_pad, c->res.regular, syn)
+                       : pick_kernel<float, 1>(c->res.dc_pad, c->res.regular, syn);
     if (!fn) return fail(LDPC_ENOTSUP, "no resident kernel for row degree %d", c->res.dc_pad);
     const int T = c->res.rows_pad;
     const size_t smem = res_smem(c, fp16);
@@ -413,7 +494,6 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
     a.NW = c->NW;
     a.T_iters = o->max_iters;
     a.early_stop = o->early_stop;
-    a.pad_slots = c->res.pad_slots ? 1 : 0;
     a.clip2 = clip_log2(o->clip);
     a.edges = c->d.res_edges;
     a.post = d_post;

@@ -51,9 +51,9 @@ struct DeviceCode {
 // shared memory (built on the host at create time).
 struct ResidentPlan {
     bool ok = false;          // the code has a resident layout
-    bool pad_slots = false;   // some bits have fewer than dv_pad edges
+    bool regular = false;     // every row has dc_pad edges and every column 3
     int32_t dc_pad = 0;       // row degree padded to an instantiated shape
-    int32_t dv_pad = 0;       // slots per bit in the bit-major message array
+    int32_t dv_pad = 0;       // message slots per bit (16-byte records)
     int32_t rows_pad = 0;     // threads per CTA of the resident launch
     std::vector<uint32_t> edges; // [cpt * ceil(dc_pad/2)][threads] 16-bit slot pairs
 };
