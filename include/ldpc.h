@@ -146,6 +146,24 @@ int ldpc_decode(const ldpc_code *code, const float *d_llr, int32_t F,
                 const ldpc_decode_opts *opts, float *d_post, uint32_t *d_hard, int32_t *d_iters,
                 uint8_t *d_ok, void *d_work, size_t work_bytes, ldpc_stream_t stream);
 
+/* The paper has no counterpart to this call.  For callers that cannot
+ * allocate device memory while decoding (for example a real-time receive
+ * thread that must not block in an allocator, or a framework that owns all
+ * device buffers): decodes exactly like ldpc_decode with LDPC_SCHED_PLAIN
+ * (opts->schedule must be LDPC_SCHED_AUTO or LDPC_SCHED_PLAIN), but takes its
+ * scratch from one static device array of LDPC_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until exit, and allocates nothing.
+ * The caller passes inputs and outputs as for ldpc_decode.  Returns
+ * LDPC_EINVAL when F frames of this code need more scratch than the array
+ * holds (ldpc_decode_workspace_size with the plain schedule gives the need).
+ * The first call on a device looks up the array's address; make it before
+ * any stream capture.  All calls share the array: calls whose work overlaps
+ * on the GPU race and must be serialised by the caller. */
+#define LDPC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int ldpc_decode_noalloc(const ldpc_code *code, const float *d_llr, int32_t F,
+                        const ldpc_decode_opts *opts, float *d_post, uint32_t *d_hard,
+                        int32_t *d_iters, uint8_t *d_ok, ldpc_stream_t stream);
+
 /* Status code to a static string. */
 const char *ldpc_status_string(int status);
 

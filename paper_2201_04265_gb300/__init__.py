@@ -22,7 +22,7 @@ from ._lib import DecodeOpts, LdpcError, QcDesc, c_i32, c_i64, c_vp
 SCHED_AUTO, SCHED_PLAIN, SCHED_RESIDENT = 0, 1, 2
 _SCHED = {"auto": SCHED_AUTO, "plain": SCHED_PLAIN, "resident": SCHED_RESIDENT}
 
-__all__ = ["Code", "encode", "syndrome", "decode", "decode_workspace_size", "DecodeResult",
+__all__ = ["Code", "encode", "syndrome", "decode", "decode_noalloc", "decode_workspace_size", "DecodeResult",
            "LdpcError", "SCHED_AUTO", "SCHED_PLAIN", "SCHED_RESIDENT"]
 
 
@@ -213,4 +213,30 @@ def decode(code: Code, llr: torch.Tensor, max_iters: int = 20, early_stop: bool 
     _lib.check(code._lib.ldpc_decode(code.handle, _ptr(llr), F, ctypes.byref(o), _ptr(out.post),
                                      _ptr(out.hard), _ptr(out.iters), _ptr(out.ok), _ptr(ws),
                                      ws.numel(), _stream_handle(stream)), "ldpc_decode")
+    return out
+
+
+def decode_noalloc(code: Code, llr: torch.Tensor, max_iters: int = 20, early_stop: bool = False,
+                   msg_fp16: bool = False, clip: float = 20.0, out: DecodeResult | None = None,
+                   want_post: bool = True, stream=None) -> DecodeResult:
+    """Plain-schedule decoding whose scratch is the library's static device array.
+
+    For callers that must not allocate device memory while decoding: the
+    library allocates nothing (pass ``out`` to make this wrapper allocate
+    nothing either).  Batches whose scratch need exceeds the array's
+    NOALLOC_SCRATCH_BYTES are rejected; concurrent calls must be serialised.
+    """
+    F = llr.shape[0]
+    _check_dev(llr, "llr", torch.float32, (F, code.n))
+    o = _opts(max_iters, early_stop, msg_fp16, SCHED_PLAIN, clip)
+    if out is None:
+        dev = llr.device
+        out = DecodeResult(
+            post=torch.empty((F, code.n), dtype=torch.float32, device=dev) if want_post else None,
+            hard=torch.empty((F, code.NW), dtype=torch.int32, device=dev),
+            iters=torch.empty((F,), dtype=torch.int32, device=dev),
+            ok=torch.empty((F,), dtype=torch.uint8, device=dev))
+    _lib.check(code._lib.ldpc_decode_noalloc(code.handle, _ptr(llr), F, ctypes.byref(o), _ptr(out.post),
+                                             _ptr(out.hard), _ptr(out.iters), _ptr(out.ok),
+                                             _stream_handle(stream)), "ldpc_decode_noalloc")
     return out

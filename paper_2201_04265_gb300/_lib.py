@@ -18,6 +18,8 @@ c_f32 = ctypes.c_float
 c_vp = ctypes.c_void_p
 c_size = ctypes.c_size_t
 
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024  # LDPC_NOALLOC_SCRATCH_BYTES in include/ldpc.h
+
 
 class LdpcError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
@@ -49,6 +51,8 @@ SIGNATURES = {
                                            ctypes.POINTER(c_size)]),
     "ldpc_decode": (c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(DecodeOpts), c_vp, c_vp, c_vp, c_vp,
                             c_vp, c_size, c_vp]),
+    "ldpc_decode_noalloc": (c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(DecodeOpts), c_vp, c_vp, c_vp, c_vp,
+                                    c_vp]),
     "ldpc_status_string": (ctypes.c_char_p, [c_i32]),
     "ldpc_last_error": (ctypes.c_char_p, []),
 }
