@@ -308,12 +308,25 @@ def run_ours(args):
 
 def _recorded_traffic():
     """DRAM bytes per launch of the resident kernel from the committed ncu
-    summary (None when no capture of the current kernel is recorded)."""
-    path = os.path.join(ROOT, "profiles", "resident_traffic.json")
-    if os.path.exists(path):
-        with open(path) as fh:
-            return json.load(fh).get("bytes_per_launch")
-    return None
+    summary, or None when the kernel source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "resident_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+    csrc = os.path.join(ROOT, "paper_2201_04265_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("decode_resident.cu", "check_math.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != rec.get("source_hash"):
+        return None
+    return int(rec["bytes_per_launch"])
 
 
 # ------------------------------------------------------- CPU oracle baseline
