@@ -146,6 +146,40 @@ int ldpc_decode(const ldpc_code *code, const float *d_llr, int32_t F,
                 const ldpc_decode_opts *opts, float *d_post, uint32_t *d_hard, int32_t *d_iters,
                 uint8_t *d_ok, void *d_work, size_t work_bytes, ldpc_stream_t stream);
 
+/* ---- Weighted belief propagation (training a decoder; not in the paper,
+ * which decodes with unit weights).  T unrolled flooding iterations in which
+ * a weight w[t][e] (T x nnz, CSR edge order, float32) multiplies the check
+ * message E_cv of edge e in iteration t in Eq. 6 and Eq. 7:
+ *   L^t_v = R_v + sum_e w[t][e] E^t_e,   bit-to-check L^t_v - w[t][e] E^t_e.
+ * With all weights 1 the result equals ldpc_decode with FP32 messages and no
+ * early stop, bit for bit. */
+
+/* Bytes of the checkpoint buffer (every iteration's messages and totals) that
+ * ldpc_wbp_forward fills and ldpc_decode_backward reads. */
+int ldpc_wbp_checkpoint_size(const ldpc_code *code, int32_t F, int32_t T, size_t *bytes);
+
+/* Forward pass: d_llr F x n, d_w T x nnz, d_post F x n receives L^T (natural
+ * units).  d_ckpt (>= ldpc_wbp_checkpoint_size bytes, 256-byte aligned) keeps
+ * the per-iteration state for the backward pass.  Row degree <= 8. */
+int ldpc_wbp_forward(const ldpc_code *code, const float *d_llr, int32_t F, int32_t T,
+                     const float *d_w, float clip, float *d_post, void *d_ckpt, size_t ckpt_bytes,
+                     ldpc_stream_t stream);
+
+/* Bytes of device workspace ldpc_decode_backward needs. */
+int ldpc_decode_backward_workspace_size(const ldpc_code *code, int32_t F, int32_t T,
+                                        size_t *bytes);
+
+/* Adjoint of ldpc_wbp_forward: given d_grad_post = dloss/dL^T (F x n),
+ * writes d_grad_w = dloss/dw (T x nnz, summed over frames in a fixed order, so
+ * repeated calls give identical bits) and, if not NULL, d_grad_llr =
+ * dloss/dR (F x n).  d_w, clip and the checkpoint must be those of the
+ * forward call.  Clipping passes the gradient on the closed range |x| <= clip
+ * and blocks it outside. */
+int ldpc_decode_backward(const ldpc_code *code, int32_t F, int32_t T, const float *d_w, float clip,
+                         const void *d_ckpt, size_t ckpt_bytes, const float *d_grad_post,
+                         float *d_grad_w, float *d_grad_llr, void *d_work, size_t work_bytes,
+                         ldpc_stream_t stream);
+
 /* The paper has no counterpart to this call.  For callers that cannot
  * allocate device memory while decoding (for example a real-time receive
  * thread that must not block in an allocator, or a framework that owns all

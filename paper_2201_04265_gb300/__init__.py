@@ -23,6 +23,7 @@ SCHED_AUTO, SCHED_PLAIN, SCHED_RESIDENT = 0, 1, 2
 _SCHED = {"auto": SCHED_AUTO, "plain": SCHED_PLAIN, "resident": SCHED_RESIDENT}
 
 __all__ = ["Code", "encode", "syndrome", "decode", "decode_noalloc", "decode_workspace_size", "DecodeResult",
+           "WeightedBP", "weighted_bp",
            "LdpcError", "SCHED_AUTO", "SCHED_PLAIN", "SCHED_RESIDENT"]
 
 
@@ -240,3 +241,55 @@ def decode_noalloc(code: Code, llr: torch.Tensor, max_iters: int = 20, early_sto
                                              _ptr(out.hard), _ptr(out.iters), _ptr(out.ok),
                                              _stream_handle(stream)), "ldpc_decode_noalloc")
     return out
+
+
+class WeightedBP(torch.autograd.Function):
+    """Weighted belief propagation with the library's hand-written adjoint.
+
+    ``WeightedBP.apply(llr, w, code, clip)``: llr float32 [F, n], w float32
+    [T, nnz] (one weight per edge and iteration, CSR edge order) -> total
+    LLRs after T iterations, float32 [F, n].  The forward keeps every
+    iteration's messages (checkpoints) for the backward pass, which returns
+    the gradients with respect to llr and w.
+    """
+
+    @staticmethod
+    def forward(ctx, llr, w, code, clip=20.0):
+        F = llr.shape[0]
+        T = w.shape[0]
+        _check_dev(llr, "llr", torch.float32, (F, code.n))
+        _check_dev(w, "w", torch.float32, (T, code.nnz))
+        nb = ctypes.c_size_t()
+        _lib.check(code._lib.ldpc_wbp_checkpoint_size(code.handle, F, T, ctypes.byref(nb)),
+                   "ldpc_wbp_checkpoint_size")
+        ckpt = _workspace(nb.value, llr.device, None)
+        post = torch.empty((F, code.n), dtype=torch.float32, device=llr.device)
+        _lib.check(code._lib.ldpc_wbp_forward(code.handle, _ptr(llr), F, T, _ptr(w), float(clip), _ptr(post),
+                                              _ptr(ckpt), ckpt.numel(), _stream_handle(None)),
+                   "ldpc_wbp_forward")
+        ctx.save_for_backward(w)
+        ctx.ckpt, ctx.code, ctx.clip, ctx.F = ckpt, code, float(clip), F
+        return post
+
+    @staticmethod
+    def backward(ctx, grad_post):
+        (w,) = ctx.saved_tensors
+        code, F, T = ctx.code, ctx.F, w.shape[0]
+        grad_post = grad_post.contiguous().to(torch.float32)
+        nb = ctypes.c_size_t()
+        _lib.check(code._lib.ldpc_decode_backward_workspace_size(code.handle, F, T, ctypes.byref(nb)),
+                   "ldpc_decode_backward_workspace_size")
+        work = _workspace(nb.value, w.device, None)
+        grad_w = torch.empty_like(w)
+        grad_llr = torch.empty((F, code.n), dtype=torch.float32, device=w.device) \
+            if ctx.needs_input_grad[0] else None
+        _lib.check(code._lib.ldpc_decode_backward(code.handle, F, T, _ptr(w), ctx.clip, _ptr(ctx.ckpt),
+                                                  ctx.ckpt.numel(), _ptr(grad_post), _ptr(grad_w),
+                                                  _ptr(grad_llr), _ptr(work), work.numel(),
+                                                  _stream_handle(None)), "ldpc_decode_backward")
+        return grad_llr, grad_w, None, None
+
+
+def weighted_bp(code: Code, llr: torch.Tensor, w: torch.Tensor, clip: float = 20.0) -> torch.Tensor:
+    """Total LLRs after ``w.shape[0]`` weighted iterations, differentiable in llr and w."""
+    return WeightedBP.apply(llr, w, code, clip)

@@ -53,6 +53,11 @@ SIGNATURES = {
                             c_vp, c_size, c_vp]),
     "ldpc_decode_noalloc": (c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(DecodeOpts), c_vp, c_vp, c_vp, c_vp,
                                     c_vp]),
+    "ldpc_wbp_checkpoint_size": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_size)]),
+    "ldpc_wbp_forward": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_f32, c_vp, c_vp, c_size, c_vp]),
+    "ldpc_decode_backward_workspace_size": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_size)]),
+    "ldpc_decode_backward": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_f32, c_vp, c_size, c_vp, c_vp, c_vp, c_vp,
+                                     c_size, c_vp]),
     "ldpc_status_string": (ctypes.c_char_p, [c_i32]),
     "ldpc_last_error": (ctypes.c_char_p, []),
 }

@@ -1,0 +1,453 @@
+// K7/K8: weighted belief propagation, forward with per-iteration checkpoints
+// and its hand-written adjoint.
+//
+// Forward (T unrolled flooding iterations, Sec. II-B with one weight per edge
+// and iteration multiplying E_cv in Eqs. 6 and 7):
+//   x^t_e = L^{t-1}_v - w_{t-1,e} E^{t-1}_e      (x^1_e = R_v; Eq. 6)
+//   E^t_e = check update of clip(x^t) over the row (Eq. 5)
+//   L^t_v = R_v + sum_e w_{t,e} E^t_e             (Eq. 7)
+// Every E^t and L^t is kept in the checkpoint buffer.  With all weights 1 the
+// arithmetic is that of the plain decoder, operation for operation.
+//
+// Backward, for t = T..1, given g(L^T) = dloss/dL^T:
+//   gL^t_v = g(L^T)_v (t = T) or sum_e gx^{t+1}_e
+//   gR_v  += gL^t_v
+//   gE^t_e = w_{t,e} (gL^t_v - gx^{t+1}_e)
+//   gw_{t,e} = sum over frames of E^t_e (gL^t_v - gx^{t+1}_e)
+//   gx^t_i = [|x_i| <= clip] sum_{j != i} gE_j [|E_j raw| <= clip] dE_j/dM_i
+// and finally gR_v += sum_e gx^1_e.  The check Jacobian uses the even/odd
+// subset-product form of check_math.cuh: with u = e^-|M|, (ev_j, od_j) the
+// pair of the row without j and Q_ij = prod_{k not i,j} (1 - u_k^2),
+//   dE_j/dM_i = (-1)^d prod_{k not i,j} sgn(M_k) * u_i Q_ij / (ev_j od_j).
+// 1 - u is formed by a Taylor series for small |M| to avoid cancellation.
+// Units: as in the decoders, LLRs are held in log2 units; this Jacobian is
+// unit-free and the weight gradient equals that in natural units.
+//
+// Layout: frame-interleaved [index][Fs] as in the plain decoder.  The weight
+// gradient is reduced over frames deterministically (warp shuffles, then the
+// warps of a block in order, then the frame blocks in order).
+#include <algorithm>
+
+#include "check_math.cuh"
+#include "ldpc_internal.h"
+
+namespace ldpc {
+namespace {
+
+constexpr int kWFB = 128;  // frames (threads) per block
+constexpr int kWMaxDeg = 8;
+
+struct WbpCkpt {
+    float *Rt;  // [n][Fs]
+    float *L;   // [T][n][Fs]   L^1..L^T
+    float *E;   // [T][E][Fs]   E^1..E^T
+    int64_t Fs;
+};
+
+size_t ckpt_layout(const ldpc_code *c, int32_t F, int32_t T, WbpCkpt *ck, void *base) {
+    const int64_t Fs = ceil_div(std::max(F, 1), 32) * 32;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off += align256(b);
+        return o;
+    };
+    const size_t oR = take((size_t)c->n * Fs * 4);
+    const size_t oL = take((size_t)T * c->n * Fs * 4);
+    const size_t oE = take((size_t)T * c->nnz * Fs * 4);
+    if (ck && base) {
+        char *b = static_cast<char *>(base);
+        ck->Rt = reinterpret_cast<float *>(b + oR);
+        ck->L = reinterpret_cast<float *>(b + oL);
+        ck->E = reinterpret_cast<float *>(b + oE);
+        ck->Fs = Fs;
+    }
+    return off;
+}
+
+struct WbpWork {
+    float *gR;      // [n][Fs]
+    float *gOut;    // [n][Fs]  dloss/dL^T in log2 units
+    float *gX;      // [E][Fs]
+    float *gE;      // [E][Fs]
+    float *gwpart;  // [nfb][E] partial weight gradients of one iteration
+    int64_t nfb;
+};
+
+size_t work_layout(const ldpc_code *c, int32_t F, WbpWork *wk, void *base) {
+    const int64_t Fs = ceil_div(std::max(F, 1), 32) * 32;
+    const int64_t nfb = ceil_div(std::max(F, 1), kWFB);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off += align256(b);
+        return o;
+    };
+    const size_t oR = take((size_t)c->n * Fs * 4);
+    const size_t oO = take((size_t)c->n * Fs * 4);
+    const size_t oX = take((size_t)c->nnz * Fs * 4);
+    const size_t oE = take((size_t)c->nnz * Fs * 4);
+    const size_t oP = take((size_t)nfb * c->nnz * 4);
+    if (wk && base) {
+        char *b = static_cast<char *>(base);
+        wk->gR = reinterpret_cast<float *>(b + oR);
+        wk->gOut = reinterpret_cast<float *>(b + oO);
+        wk->gX = reinterpret_cast<float *>(b + oX);
+        wk->gE = reinterpret_cast<float *>(b + oE);
+        wk->gwpart = reinterpret_cast<float *>(b + oP);
+        wk->nfb = nfb;
+    }
+    return off;
+}
+
+// llr[F][n] (natural units) -> dst[n][Fs] scaled by `scale`.
+__global__ void to_interleaved(const float *__restrict__ src, float *__restrict__ dst, int32_t n,
+                               int32_t F, int64_t Fs, float scale) {
+    __shared__ float tile[32][33];
+    const int64_t v0 = (int64_t)blockIdx.x * 32, f0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t f = f0 + i, v = v0 + threadIdx.x;
+        tile[i][threadIdx.x] = (f < F && v < n) ? src[f * n + v] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t v = v0 + i, f = f0 + threadIdx.x;
+        if (v < n && f < F) dst[v * Fs + f] = tile[threadIdx.x][i] * scale;
+    }
+}
+
+// src[n][Fs] -> dst[F][n] scaled by `scale`.
+__global__ void from_interleaved(const float *__restrict__ src, float *__restrict__ dst, int32_t n,
+                                 int32_t F, int64_t Fs, float scale) {
+    __shared__ float tile[32][33];
+    const int64_t v0 = (int64_t)blockIdx.x * 32, f0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t v = v0 + i, f = f0 + threadIdx.x;
+        tile[i][threadIdx.x] = (v < n && f < F) ? src[v * Fs + f] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t f = f0 + i, v = v0 + threadIdx.x;
+        if (f < F && v < n) dst[f * n + v] = tile[threadIdx.x][i] * scale;
+    }
+}
+
+// Forward check update of iteration t (inputs from the previous checkpoint).
+template <int DMAX>
+__global__ void __launch_bounds__(kWFB)
+wbp_check(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
+          const float *__restrict__ wprev, float *__restrict__ Ecur,
+          const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int32_t m,
+          int32_t F, int64_t Fs, float clip2) {
+    const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
+    const int c = blockIdx.x;
+    if (f >= F || c >= m) return;
+    const int e0 = __ldg(&row_ptr[c]);
+    const int d = __ldg(&row_ptr[c + 1]) - e0;
+    float u[DMAX];
+    uint32_t xb[DMAX], sacc = (uint32_t)(d & 1) << 31;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < d) {
+            const int e = e0 + j;
+            const float L = Lprev[(int64_t)__ldg(&col_idx[e]) * Fs + f];
+            const float x = Eprev ? fmaf(-__ldg(&wprev[e]), Eprev[(int64_t)e * Fs + f], L) : L;
+            xb[j] = __float_as_uint(x);
+            sacc ^= xb[j];
+            u[j] = check_u(fminf(fmaxf(x, -clip2), clip2));
+        }
+    }
+    EvOd pre[DMAX];
+    pre[0] = {1.f, 0.f};
+#pragma unroll
+    for (int j = 1; j < DMAX; ++j)
+        if (j < d) pre[j] = evod_add(pre[j - 1], u[j - 1]);
+    EvOd suf = {1.f, 0.f};
+#pragma unroll
+    for (int j = DMAX - 1; j >= 0; --j) {
+        if (j < d) {
+            const float mag = evod_magnitude(evod_join(pre[j], suf), clip2);
+            Ecur[(int64_t)(e0 + j) * Fs + f] =
+                __uint_as_float(__float_as_uint(mag) | ((sacc ^ xb[j]) & 0x80000000u));
+            suf = evod_add(suf, u[j]);
+        }
+    }
+}
+
+// Forward bit update of iteration t: L^t_v = R_v + sum_e w_{t,e} E^t_e.
+__global__ void __launch_bounds__(kWFB)
+wbp_bit(const float *__restrict__ Rt, const float *__restrict__ Ecur, const float *__restrict__ wcur,
+        float *__restrict__ Lcur, const int32_t *__restrict__ col_ptr,
+        const int32_t *__restrict__ col_edge, int32_t n, int32_t F, int64_t Fs) {
+    const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
+    const int v = blockIdx.x;
+    if (f >= F || v >= n) return;
+    float L = Rt[(int64_t)v * Fs + f];
+    for (int q = __ldg(&col_ptr[v]), q1 = __ldg(&col_ptr[v + 1]); q < q1; ++q) {
+        const int e = __ldg(&col_edge[q]);
+        L = fmaf(__ldg(&wcur[e]), Ecur[(int64_t)e * Fs + f], L);
+    }
+    Lcur[(int64_t)v * Fs + f] = L;
+}
+
+// 1 - 2^-y for y >= 0 without cancellation near y = 0.
+__device__ __forceinline__ float one_minus_exp2neg(float y, float u) {
+    if (y >= 0.25f) return 1.f - u;
+    const float z = y * kLn2;  // 1 - e^-z = z - z^2/2 + z^3/6 - z^4/24 + z^5/120 - ...
+    return z * (1.f + z * (-0.5f + z * (1.f / 6.f + z * (-1.f / 24.f + z * (1.f / 120.f)))));
+}
+
+// Backward bit side of iteration t.  Accumulates gR, forms gE^t and the
+// weight-gradient contributions, reduced over the block's frames into
+// gwpart[blockIdx.y][e].
+__global__ void __launch_bounds__(kWFB)
+wbp_bit_back(const float *__restrict__ gout2, const float *__restrict__ gX,
+             const float *__restrict__ Ecur, const float *__restrict__ wcur, float *__restrict__ gE,
+             float *__restrict__ gR, float *__restrict__ gwpart, const int32_t *__restrict__ col_ptr,
+             const int32_t *__restrict__ col_edge, int32_t n, int32_t F, int64_t Fs, int last,
+             int first_acc, int32_t nnz) {
+    __shared__ float red[kWFB / 32];
+    const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
+    const int v = blockIdx.x;
+    const bool live = f < F;
+    const int q0 = __ldg(&col_ptr[v]), q1 = __ldg(&col_ptr[v + 1]);
+    float gL = 0.f;
+    if (live) {
+        if (last) {
+            gL = gout2[(int64_t)v * Fs + f];
+        } else {
+            for (int q = q0; q < q1; ++q) gL += gX[(int64_t)__ldg(&col_edge[q]) * Fs + f];
+        }
+        const int64_t iv = (int64_t)v * Fs + f;
+        gR[iv] = first_acc ? gL : gR[iv] + gL;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = q0; q < q1; ++q) {
+        const int e = __ldg(&col_edge[q]);
+        float contrib = 0.f;
+        if (live) {
+            const int64_t ie = (int64_t)e * Fs + f;
+            const float g = last ? gL : gL - gX[ie];
+            gE[ie] = __ldg(&wcur[e]) * g;
+            contrib = Ecur[ie] * g;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
+        if (lane == 0) red[warp] = contrib;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float s = 0.f;
+            for (int w = 0; w < kWFB / 32; ++w) s += red[w];
+            gwpart[(int64_t)blockIdx.y * nnz + e] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Backward check side of iteration t: gx^t from gE^t through the check
+// Jacobian, with the clip masks.
+template <int DMAX>
+__global__ void __launch_bounds__(kWFB)
+wbp_check_back(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
+               const float *__restrict__ wprev, const float *__restrict__ gE,
+               float *__restrict__ gX, const int32_t *__restrict__ row_ptr,
+               const int32_t *__restrict__ col_idx, int32_t m, int32_t F, int64_t Fs, float clip2) {
+    const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
+    const int c = blockIdx.x;
+    if (f >= F || c >= m) return;
+    const int e0 = __ldg(&row_ptr[c]);
+    const int d = __ldg(&row_ptr[c + 1]) - e0;
+    float u[DMAX], q[DMAX], h[DMAX];
+    uint32_t sgn = 0, inmask = 0;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < d) {
+            const int e = e0 + j;
+            const float L = Lprev[(int64_t)__ldg(&col_idx[e]) * Fs + f];
+            const float x = Eprev ? fmaf(-__ldg(&wprev[e]), Eprev[(int64_t)e * Fs + f], L) : L;
+            sgn |= (__float_as_uint(x) >> 31) << j;
+            inmask |= (uint32_t)(fabsf(x) <= clip2) << j;
+            const float y = fminf(fabsf(x), clip2);
+            u[j] = check_u(y);
+            q[j] = one_minus_exp2neg(y, u[j]) * (1.f + u[j]);
+        } else {
+            u[j] = 0.f;
+            q[j] = 1.f;
+        }
+    }
+    // leave-one-out pairs as in the forward, to get ev_j od_j and the output mask
+    EvOd pre[DMAX];
+    pre[0] = {1.f, 0.f};
+#pragma unroll
+    for (int j = 1; j < DMAX; ++j)
+        if (j < d) pre[j] = evod_add(pre[j - 1], u[j - 1]);
+    EvOd suf = {1.f, 0.f};
+#pragma unroll
+    for (int j = DMAX - 1; j >= 0; --j) {
+        h[j] = 0.f;
+        if (j < d) {
+            const EvOd p = evod_join(pre[j], suf);
+            const float raw = lg2_approx(p.e * rcp_approx(p.o));
+            if (raw <= clip2 && p.o > 0.f) h[j] = gE[(int64_t)(e0 + j) * Fs + f] / (p.e * p.o);
+            suf = evod_add(suf, u[j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i) {
+        if (i >= d) continue;
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) {
+            if (j >= d || j == i) continue;
+            float Q = 1.f;
+#pragma unroll
+            for (int k = 0; k < DMAX; ++k)
+                if (k != i && k != j) Q *= q[k];
+            const uint32_t s = (__popc(sgn & ~((1u << i) | (1u << j))) + d) & 1u;
+            acc += s ? -h[j] * Q : h[j] * Q;
+        }
+        gX[(int64_t)(e0 + i) * Fs + f] = ((inmask >> i) & 1u) ? u[i] * acc : 0.f;
+    }
+}
+
+// gR_v += sum_e gx^1_e (x^1 = R).
+__global__ void wbp_final_r(const float *__restrict__ gX, float *__restrict__ gR,
+                            const int32_t *__restrict__ col_ptr, const int32_t *__restrict__ col_edge,
+                            int32_t n, int32_t F, int64_t Fs) {
+    const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
+    const int v = blockIdx.x;
+    if (f >= F || v >= n) return;
+    float s = gR[(int64_t)v * Fs + f];
+    for (int q = __ldg(&col_ptr[v]), q1 = __ldg(&col_ptr[v + 1]); q < q1; ++q)
+        s += gX[(int64_t)__ldg(&col_edge[q]) * Fs + f];
+    gR[(int64_t)v * Fs + f] = s;
+}
+
+// grad_w[t][e] = sum over frame blocks (in order) of the partials.
+__global__ void wbp_reduce_w(const float *__restrict__ gwpart, float *__restrict__ gw, int64_t nfb,
+                             int32_t nnz) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    float s = 0.f;
+    for (int64_t b = 0; b < nfb; ++b) s += gwpart[b * nnz + e];
+    gw[e] = s;
+}
+
+int check_wbp_args(const ldpc_code *c, int32_t F, int32_t T, float clip) {
+    if (!c) return fail(LDPC_EINVAL, "code is NULL");
+    if (!c->on_device) return fail(LDPC_EINVAL, "code was created host-only");
+    if (F < 0 || T < 0) return fail(LDPC_EINVAL, "F and T must be >= 0");
+    if (!(clip > 0.f)) return fail(LDPC_EINVAL, "clip must be positive");
+    if (c->dc_max > kWMaxDeg) return fail(LDPC_ENOTSUP, "weighted BP supports row degree <= %d", kWMaxDeg);
+    if (ceil_div(F, kWFB) > 65535) return fail(LDPC_ENOTSUP, "too many frames (F=%d)", F);
+    return LDPC_OK;
+}
+
+}  // namespace
+}  // namespace ldpc
+
+using namespace ldpc;
+
+extern "C" {
+
+int ldpc_wbp_checkpoint_size(const ldpc_code *c, int32_t F, int32_t T, size_t *bytes) {
+    if (!c || !bytes || F < 0 || T < 0) return fail(LDPC_EINVAL, "bad arguments");
+    *bytes = ckpt_layout(c, F, T, nullptr, nullptr);
+    return LDPC_OK;
+}
+
+int ldpc_wbp_forward(const ldpc_code *c, const float *d_llr, int32_t F, int32_t T, const float *d_w,
+                     float clip, float *d_post, void *d_ckpt, size_t ckpt_bytes,
+                     ldpc_stream_t stream) {
+    LDPC_TRY(check_wbp_args(c, F, T, clip));
+    if (F == 0) return LDPC_OK;
+    if (!d_llr || !d_post || !d_ckpt || (T > 0 && !d_w)) return fail(LDPC_EINVAL, "NULL pointer");
+    WbpCkpt ck{};
+    const size_t need = ckpt_layout(c, F, T, &ck, d_ckpt);
+    if (ckpt_bytes < need) return fail(LDPC_EINVAL, "checkpoint buffer too small (%zu < %zu)", ckpt_bytes, need);
+    cudaStream_t s = (cudaStream_t)stream;
+    const float clip2 = clip_log2(clip);
+    const dim3 tgrid((unsigned)ceil_div(c->n, 32), (unsigned)ceil_div(F, 32));
+    to_interleaved<<<tgrid, dim3(32, 8), 0, s>>>(d_llr, ck.Rt, c->n, F, ck.Fs, kLog2e);
+    const size_t nF = (size_t)c->n * ck.Fs, eF = (size_t)c->nnz * ck.Fs;
+    for (int t = 1; t <= T; ++t) {
+        const float *Lprev = t == 1 ? ck.Rt : ck.L + (t - 2) * nF;
+        const float *Eprev = t == 1 ? nullptr : ck.E + (t - 2) * eF;
+        const float *wprev = t == 1 ? nullptr : d_w + (size_t)(t - 2) * c->nnz;
+        float *Ecur = ck.E + (t - 1) * eF;
+        float *Lcur = ck.L + (t - 1) * nF;
+        const dim3 cg((unsigned)c->m, (unsigned)ceil_div(F, kWFB));
+        wbp_check<kWMaxDeg><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, Ecur, c->d.row_ptr, c->d.col_idx,
+                                                c->m, F, ck.Fs, clip2);
+        const dim3 bg((unsigned)c->n, (unsigned)ceil_div(F, kWFB));
+        wbp_bit<<<bg, kWFB, 0, s>>>(ck.Rt, Ecur, d_w + (size_t)(t - 1) * c->nnz, Lcur, c->d.col_ptr,
+                                    c->d.col_edge, c->n, F, ck.Fs);
+    }
+    if (T == 0) {
+        LDPC_TRY_CUDA(cudaMemcpyAsync(d_post, d_llr, sizeof(float) * (size_t)F * c->n,
+                                      cudaMemcpyDeviceToDevice, s));
+    } else {
+        from_interleaved<<<tgrid, dim3(32, 8), 0, s>>>(ck.L + (T - 1) * nF, d_post, c->n, F, ck.Fs, kLn2);
+    }
+    LDPC_TRY_CUDA(cudaGetLastError());
+    return LDPC_OK;
+}
+
+int ldpc_decode_backward_workspace_size(const ldpc_code *c, int32_t F, int32_t T, size_t *bytes) {
+    if (!c || !bytes || F < 0 || T < 0) return fail(LDPC_EINVAL, "bad arguments");
+    *bytes = work_layout(c, F, nullptr, nullptr);
+    return LDPC_OK;
+}
+
+int ldpc_decode_backward(const ldpc_code *c, int32_t F, int32_t T, const float *d_w, float clip,
+                         const void *d_ckpt, size_t ckpt_bytes,
+                         const float *d_grad_post, float *d_grad_w, float *d_grad_llr, void *d_work,
+                         size_t work_bytes, ldpc_stream_t stream) {
+    LDPC_TRY(check_wbp_args(c, F, T, clip));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (T > 0 && d_grad_w && F == 0)
+        LDPC_TRY_CUDA(cudaMemsetAsync(d_grad_w, 0, sizeof(float) * (size_t)T * c->nnz, s));
+    if (F == 0) return LDPC_OK;
+    if (!d_ckpt || !d_grad_post || (T > 0 && !d_w)) return fail(LDPC_EINVAL, "NULL pointer");
+    WbpCkpt ck{};
+    if (ckpt_bytes < ckpt_layout(c, F, T, &ck, const_cast<void *>(d_ckpt)))
+        return fail(LDPC_EINVAL, "checkpoint buffer too small");
+    WbpWork wk{};
+    const size_t need = work_layout(c, F, &wk, d_work);
+    if (!d_work || work_bytes < need) return fail(LDPC_EINVAL, "workspace too small (%zu < %zu)", work_bytes, need);
+    const float clip2 = clip_log2(clip);
+    const dim3 tgrid((unsigned)ceil_div(c->n, 32), (unsigned)ceil_div(F, 32));
+    if (T == 0) {  // post = llr: the gradient passes straight through
+        if (d_grad_llr)
+            LDPC_TRY_CUDA(cudaMemcpyAsync(d_grad_llr, d_grad_post, sizeof(float) * (size_t)F * c->n,
+                                          cudaMemcpyDeviceToDevice, s));
+        return LDPC_OK;
+    }
+    // dloss/dL2 = dloss/dpost * ln 2 (post = L2 ln 2)
+    to_interleaved<<<tgrid, dim3(32, 8), 0, s>>>(d_grad_post, wk.gOut, c->n, F, ck.Fs, kLn2);
+    float *gX = wk.gX;
+    const size_t nF = (size_t)c->n * ck.Fs, eF = (size_t)c->nnz * ck.Fs;
+    const dim3 bg((unsigned)c->n, (unsigned)ceil_div(F, kWFB));
+    const dim3 cg((unsigned)c->m, (unsigned)ceil_div(F, kWFB));
+    for (int t = T; t >= 1; --t) {
+        const float *Ecur = ck.E + (t - 1) * eF;
+        const float *wcur = d_w + (size_t)(t - 1) * c->nnz;
+        wbp_bit_back<<<bg, kWFB, 0, s>>>(wk.gOut, gX, Ecur, wcur, wk.gE, wk.gR, wk.gwpart, c->d.col_ptr,
+                                         c->d.col_edge, c->n, F, ck.Fs, t == T, t == T, (int32_t)c->nnz);
+        if (d_grad_w)
+            wbp_reduce_w<<<(unsigned)ceil_div(c->nnz, 256), 256, 0, s>>>(
+                wk.gwpart, d_grad_w + (size_t)(t - 1) * c->nnz, wk.nfb, (int32_t)c->nnz);
+        const float *Lprev = t == 1 ? ck.Rt : ck.L + (t - 2) * nF;
+        const float *Eprev = t == 1 ? nullptr : ck.E + (t - 2) * eF;
+        const float *wprev = t == 1 ? nullptr : d_w + (size_t)(t - 2) * c->nnz;
+        wbp_check_back<kWMaxDeg><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, wk.gE, gX, c->d.row_ptr,
+                                                     c->d.col_idx, c->m, F, ck.Fs, clip2);
+    }
+    wbp_final_r<<<bg, kWFB, 0, s>>>(gX, wk.gR, c->d.col_ptr, c->d.col_edge, c->n, F, ck.Fs);
+    if (d_grad_llr)
+        from_interleaved<<<tgrid, dim3(32, 8), 0, s>>>(wk.gR, d_grad_llr, c->n, F, ck.Fs, kLog2e);
+    LDPC_TRY_CUDA(cudaGetLastError());
+    return LDPC_OK;
+}
+
+}  // extern "C"
