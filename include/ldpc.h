@@ -146,6 +146,56 @@ int ldpc_decode(const ldpc_code *code, const float *d_llr, int32_t F,
                 const ldpc_decode_opts *opts, float *d_post, uint32_t *d_hard, int32_t *d_iters,
                 uint8_t *d_ok, void *d_work, size_t work_bytes, ldpc_stream_t stream);
 
+/* ---- Mixed-code batches (serving): frames of several codes decoded in one
+ * persistent launch.  A plan holds the codes (each regular with column weight
+ * 3 and row weight 6, 9 or 12, at most 8192 bits, e.g. rates 1/2, 2/3, 3/4)
+ * and a launch configuration.  ldpc_decode_mixed queues only device work
+ * (memsets and kernels) on the stream, so it can be captured in a CUDA graph
+ * and replayed; the same frame decoded alone by ldpc_decode gives the same
+ * bits, whatever the configuration. */
+typedef struct ldpc_mixed ldpc_mixed;
+
+#define LDPC_MIXED_ORDER_LARGEST_FIRST 0 /* work on codes with most edges first */
+#define LDPC_MIXED_ORDER_GIVEN 1         /* codes in the order given */
+
+typedef struct {
+    int32_t order;           /* LDPC_MIXED_ORDER_* */
+    int32_t groups_per_item; /* frame groups each team takes per work item (1..64) */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM (1..4, capped by occupancy) */
+} ldpc_mixed_config;
+
+/* codes[ncodes]: code objects on the current device (they must outlive the
+ * plan).  msg_fp16 as in ldpc_decode_opts.  Synchronous; allocates the
+ * plan's device tables. */
+int ldpc_mixed_create(const ldpc_code *const *codes, int32_t ncodes, int32_t msg_fp16,
+                      ldpc_mixed **out);
+void ldpc_mixed_destroy(ldpc_mixed *plan);
+int ldpc_mixed_workspace_size(const ldpc_mixed *plan, int32_t F, size_t *bytes);
+int ldpc_mixed_get_config(const ldpc_mixed *plan, ldpc_mixed_config *cfg);
+int ldpc_mixed_set_config(ldpc_mixed *plan, const ldpc_mixed_config *cfg);
+
+/* Decodes F frames; frame f uses code d_frame_code[f] (an index into the
+ * plan's codes), reads its n_f channel LLRs at d_llr + d_llr_off[f], writes its
+ * total LLRs (if d_post) at d_post + d_llr_off[f] and its packed hard decisions
+ * (if d_hard) at d_hard + d_hard_off[f] (ceil(n_f/32) words), and d_iters[f],
+ * d_ok[f] (each may be NULL).  A frame whose code index is out of range is not
+ * decoded and gets iters = -1, ok = 0.  Options as in ldpc_decode_opts. */
+int ldpc_decode_mixed(const ldpc_mixed *plan, const int32_t *d_frame_code, const int64_t *d_llr_off,
+                      const int64_t *d_hard_off, const float *d_llr, int32_t F, int32_t max_iters,
+                      int32_t early_stop, float clip, float *d_post, uint32_t *d_hard,
+                      int32_t *d_iters, uint8_t *d_ok, void *d_work, size_t work_bytes,
+                      ldpc_stream_t stream);
+
+/* Autotuner: decodes the given batch with every candidate configuration
+ * (work order x groups per item x CTAs per SM), times `reps` runs of each with
+ * CUDA events, keeps the fastest in the plan and returns it in *chosen.
+ * Synchronises the stream; outputs hold the last run's (identical) results. */
+int ldpc_mixed_autotune(ldpc_mixed *plan, const int32_t *d_frame_code, const int64_t *d_llr_off,
+                        const int64_t *d_hard_off, const float *d_llr, int32_t F, int32_t max_iters,
+                        int32_t early_stop, float clip, float *d_post, uint32_t *d_hard,
+                        int32_t *d_iters, uint8_t *d_ok, void *d_work, size_t work_bytes,
+                        int32_t reps, ldpc_stream_t stream, ldpc_mixed_config *chosen);
+
 /* ---- Weighted belief propagation (training a decoder; not in the paper,
  * which decodes with unit weights).  T unrolled flooding iterations in which
  * a weight w[t][e] (T x nnz, CSR edge order, float32) multiplies the check

@@ -23,7 +23,7 @@ SCHED_AUTO, SCHED_PLAIN, SCHED_RESIDENT = 0, 1, 2
 _SCHED = {"auto": SCHED_AUTO, "plain": SCHED_PLAIN, "resident": SCHED_RESIDENT}
 
 __all__ = ["Code", "encode", "syndrome", "decode", "decode_noalloc", "decode_workspace_size", "DecodeResult",
-           "WeightedBP", "weighted_bp",
+           "WeightedBP", "weighted_bp", "MixedPlan", "MixedBatch",
            "LdpcError", "SCHED_AUTO", "SCHED_PLAIN", "SCHED_RESIDENT"]
 
 
@@ -293,3 +293,95 @@ class WeightedBP(torch.autograd.Function):
 def weighted_bp(code: Code, llr: torch.Tensor, w: torch.Tensor, clip: float = 20.0) -> torch.Tensor:
     """Total LLRs after ``w.shape[0]`` weighted iterations, differentiable in llr and w."""
     return WeightedBP.apply(llr, w, code, clip)
+
+
+@dataclass
+class MixedBatch:
+    """Device-side description of a mixed-code batch (see MixedPlan.batch)."""
+    frame_code: torch.Tensor  # int32 [F]
+    llr_off: torch.Tensor     # int64 [F], element offset of each frame's LLRs (and posterior)
+    hard_off: torch.Tensor    # int64 [F], word offset of each frame's hard decisions
+    n_llr: int                # total LLR elements
+    n_hard: int               # total hard-decision words
+
+
+class MixedPlan:
+    """Several codes decoded in one persistent launch (ldpc_mixed_* in the C ABI)."""
+
+    def __init__(self, codes, msg_fp16: bool = True):
+        self._lib = _lib.load()
+        self.codes = list(codes)
+        arr = (c_vp * len(self.codes))(*[c.handle.value for c in self.codes])
+        self._h = c_vp(None)
+        _lib.check(self._lib.ldpc_mixed_create(arr, len(self.codes), int(bool(msg_fp16)), ctypes.byref(self._h)),
+                   "ldpc_mixed_create")
+
+    def close(self):
+        if self._h:
+            self._lib.ldpc_mixed_destroy(self._h)
+            self._h = c_vp(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def batch(self, frame_code, device="cuda") -> MixedBatch:
+        """Offsets for frames laid out back to back in frame order."""
+        fc = np.asarray(frame_code, dtype=np.int32)
+        ns = np.array([self.codes[c].n for c in fc], dtype=np.int64)
+        nws = (ns + 31) // 32
+        llr_off = np.concatenate([[0], np.cumsum(ns)[:-1]]) if len(fc) else np.zeros(0, np.int64)
+        hard_off = np.concatenate([[0], np.cumsum(nws)[:-1]]) if len(fc) else np.zeros(0, np.int64)
+        return MixedBatch(torch.from_numpy(fc).to(device), torch.from_numpy(llr_off.astype(np.int64)).to(device),
+                          torch.from_numpy(hard_off.astype(np.int64)).to(device), int(ns.sum()), int(nws.sum()))
+
+    def config(self) -> dict:
+        cfg = _lib.MixedConfig()
+        _lib.check(self._lib.ldpc_mixed_get_config(self._h, ctypes.byref(cfg)), "ldpc_mixed_get_config")
+        return {"order": cfg.order, "groups_per_item": cfg.groups_per_item, "ctas_per_sm": cfg.ctas_per_sm}
+
+    def set_config(self, order: int = 0, groups_per_item: int = 1, ctas_per_sm: int = 1) -> None:
+        cfg = _lib.MixedConfig(order, groups_per_item, ctas_per_sm)
+        _lib.check(self._lib.ldpc_mixed_set_config(self._h, ctypes.byref(cfg)), "ldpc_mixed_set_config")
+
+    def workspace(self, F: int, device="cuda") -> torch.Tensor:
+        nb = ctypes.c_size_t()
+        _lib.check(self._lib.ldpc_mixed_workspace_size(self._h, int(F), ctypes.byref(nb)), "ldpc_mixed_workspace_size")
+        return _workspace(nb.value, device, None)
+
+    def outputs(self, b: MixedBatch, want_post: bool = True, device="cuda") -> DecodeResult:
+        F = b.frame_code.shape[0]
+        return DecodeResult(
+            post=torch.empty((b.n_llr,), dtype=torch.float32, device=device) if want_post else None,
+            hard=torch.empty((b.n_hard,), dtype=torch.int32, device=device),
+            iters=torch.empty((F,), dtype=torch.int32, device=device),
+            ok=torch.empty((F,), dtype=torch.uint8, device=device))
+
+    def _args(self, b, llr, max_iters, early_stop, clip, out, ws):
+        return (self._h, _ptr(b.frame_code), _ptr(b.llr_off), _ptr(b.hard_off), _ptr(llr), b.frame_code.shape[0],
+                int(max_iters), int(bool(early_stop)), float(clip), _ptr(out.post), _ptr(out.hard),
+                _ptr(out.iters), _ptr(out.ok), _ptr(ws), ws.numel())
+
+    def decode(self, b: MixedBatch, llr: torch.Tensor, max_iters: int = 50, early_stop: bool = True,
+               clip: float = 20.0, out: DecodeResult | None = None, workspace: torch.Tensor | None = None,
+               stream=None) -> DecodeResult:
+        """Decodes the batch; with ``out`` and ``workspace`` given it queues device
+        work only (memsets and kernels), so it can be captured in a CUDA graph."""
+        _check_dev(llr, "llr", torch.float32, (b.n_llr,))
+        out = out if out is not None else self.outputs(b, device=llr.device)
+        ws = workspace if workspace is not None else self.workspace(b.frame_code.shape[0], llr.device)
+        _lib.check(self._lib.ldpc_decode_mixed(*self._args(b, llr, max_iters, early_stop, clip, out, ws),
+                                               _stream_handle(stream)), "ldpc_decode_mixed")
+        return out
+
+    def autotune(self, b: MixedBatch, llr: torch.Tensor, max_iters: int = 50, early_stop: bool = True,
+                 clip: float = 20.0, reps: int = 3, stream=None) -> dict:
+        out = self.outputs(b, device=llr.device)
+        ws = self.workspace(b.frame_code.shape[0], llr.device)
+        cfg = _lib.MixedConfig()
+        _lib.check(self._lib.ldpc_mixed_autotune(*self._args(b, llr, max_iters, early_stop, clip, out, ws),
+                                                 int(reps), _stream_handle(stream), ctypes.byref(cfg)),
+                   "ldpc_mixed_autotune")
+        return {"order": cfg.order, "groups_per_item": cfg.groups_per_item, "ctas_per_sm": cfg.ctas_per_sm}

@@ -31,6 +31,10 @@ class QcDesc(ctypes.Structure):
     _fields_ = [("mb", c_i32), ("nb", c_i32), ("z", c_i32), ("shift", ctypes.POINTER(ctypes.c_int16))]
 
 
+class MixedConfig(ctypes.Structure):
+    _fields_ = [("order", c_i32), ("groups_per_item", c_i32), ("ctas_per_sm", c_i32)]
+
+
 class DecodeOpts(ctypes.Structure):
     _fields_ = [("max_iters", c_i32), ("early_stop", c_i32), ("msg_fp16", c_i32),
                 ("schedule", c_i32), ("clip", c_f32)]
@@ -58,6 +62,15 @@ SIGNATURES = {
     "ldpc_decode_backward_workspace_size": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_size)]),
     "ldpc_decode_backward": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_f32, c_vp, c_size, c_vp, c_vp, c_vp, c_vp,
                                      c_size, c_vp]),
+    "ldpc_mixed_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, c_i32, ctypes.POINTER(c_vp)]),
+    "ldpc_mixed_destroy": (None, [c_vp]),
+    "ldpc_mixed_workspace_size": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_size)]),
+    "ldpc_mixed_get_config": (c_i32, [c_vp, ctypes.POINTER(MixedConfig)]),
+    "ldpc_mixed_set_config": (c_i32, [c_vp, ctypes.POINTER(MixedConfig)]),
+    "ldpc_decode_mixed": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_i32, c_f32, c_vp, c_vp, c_vp,
+                                  c_vp, c_vp, c_size, c_vp]),
+    "ldpc_mixed_autotune": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_i32, c_f32, c_vp, c_vp, c_vp,
+                                    c_vp, c_vp, c_size, c_i32, c_vp, ctypes.POINTER(MixedConfig)]),
     "ldpc_status_string": (ctypes.c_char_p, [c_i32]),
     "ldpc_last_error": (ctypes.c_char_p, []),
 }

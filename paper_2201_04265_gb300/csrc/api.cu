@@ -1,7 +1,53 @@
 // Entry points of the C ABI that launch work: argument checks and dispatch.
 #include "ldpc_internal.h"
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 namespace ldpc {
+
+int kernel_setup(const void *fn, int threads, size_t smem, int *per_sm) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, size_t>, int> cache;  // (fn, dev, threads, smem)
+    static std::map<std::pair<const void *, int>, size_t> smem_set;          // (fn, dev) -> limit
+    int dev = -1;
+    LDPC_TRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(fn, dev, threads, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        if (per_sm) *per_sm = it->second;
+        return LDPC_OK;
+    }
+    size_t &lim = smem_set[std::make_pair(fn, dev)];
+    if (smem > 48 * 1024 && smem > lim) {
+        LDPC_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        lim = smem;
+    }
+    int n = 0;
+    LDPC_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem));
+    cache[key] = n;
+    if (per_sm) *per_sm = n;
+    return LDPC_OK;
+}
+
+int sm_count(int *sms) {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = -1;
+    LDPC_TRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(dev);
+    if (it == cache.end()) {
+        int n = 0;
+        LDPC_TRY_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        it = cache.emplace(dev, n).first;
+    }
+    *sms = it->second;
+    return LDPC_OK;
+}
+
 int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_decode_opts *o,
                     float *d_post, uint32_t *d_hard, int32_t *d_iters, uint8_t *d_ok, void *d_work,
                     size_t work_bytes, cudaStream_t s);

@@ -130,8 +130,7 @@ template <int FT>
 int launch_enc(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, int32_t F,
                cudaStream_t s) {
     const size_t sm = enc_smem<FT>(c);
-    LDPC_TRY_CUDA(cudaFuncSetAttribute(encode_kernel<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm));
+    LDPC_TRY(kernel_setup((const void *)encode_kernel<FT>, kEncThreads, sm, nullptr));
     const unsigned grid = (unsigned)ceil_div(F, FT);
     encode_kernel<FT><<<grid, kEncThreads, sm, s>>>(d_info, d_code, c->d.AT, c->d.info_pos,
                                                    c->d.parity_pos, F, c->k, c->rank, c->KW, c->NW);
@@ -154,11 +153,9 @@ int launch_syndrome(const ldpc_code *c, const uint32_t *d_bits, int32_t F, uint3
                     uint8_t *d_ok, cudaStream_t s) {
     const size_t sm = (size_t)c->NW * sizeof(uint32_t);
     if (sm > 200 * 1024) return fail(LDPC_ENOTSUP, "code too long for the syndrome kernel");
-    LDPC_TRY_CUDA(cudaFuncSetAttribute(syndrome_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)std::max<size_t>(sm, 1)));
-    int dev = 0, sms = 0;
-    LDPC_TRY_CUDA(cudaGetDevice(&dev));
-    LDPC_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LDPC_TRY(kernel_setup((const void *)syndrome_kernel, 256, sm, nullptr));
+    int sms = 0;
+    LDPC_TRY(sm_count(&sms));
     const unsigned grid = (unsigned)std::min<int64_t>(F, (int64_t)sms * 8);
     syndrome_kernel<<<grid, 256, sm, s>>>(d_bits, F, c->m, c->NW, c->MW, c->d.row_ptr, c->d.col_idx,
                                           d_syn, d_ok);

@@ -74,6 +74,11 @@ struct ldpc_code {
 };
 
 namespace ldpc {
+// Sets a kernel's dynamic shared-memory limit (once per kernel and device)
+// and returns its resident CTAs per SM for the launch shape (cached), so that
+// launchers make no attribute calls on the repeat calls a CUDA graph captures.
+int kernel_setup(const void *fn, int threads, size_t smem, int *per_sm);
+int sm_count(int *sms);
 // Kernel launchers (defined in the .cu files).
 int launch_encode(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, int32_t F,
                   cudaStream_t s);
