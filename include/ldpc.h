@@ -90,6 +90,15 @@ int ldpc_code_positions(const ldpc_code *code, int32_t *info_pos, int32_t *parit
  * is the coefficient of information bit i in parity bit j (Eq. 3). */
 int ldpc_code_parity_map(const ldpc_code *code, uint32_t *A);
 
+/* Host copy of each check's evaluation order: eval_edge[row_ptr[c] + j] is the
+ * CSR edge id of the j-th input check c combines (every decoder uses this
+ * order, chosen at creation so that the shared-memory gathers of the resident
+ * decoders are free of bank conflicts), and *unplaced the number of edges the
+ * schedule could not place conflict-free (0 when every warp step touches 32
+ * distinct banks).  The paper has no counterpart (the order of the inputs of
+ * Eq. 5 does not change its value).  Either pointer may be NULL. */
+int ldpc_code_schedule(const ldpc_code *code, int32_t *eval_edge, int64_t *unplaced);
+
 /* Frees the code; NULL is ignored.  Must not race with work still queued
  * that uses it (synchronise the streams first). */
 void ldpc_code_destroy(ldpc_code *code);

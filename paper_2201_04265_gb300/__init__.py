@@ -113,6 +113,14 @@ class Code:
         _lib.check(self._lib.ldpc_code_parity_map(self.handle, c_vp(a.ctypes.data)), "ldpc_code_parity_map")
         return a[:self.rank]
 
+    def schedule(self) -> tuple[np.ndarray, int]:
+        """(evaluation order as CSR edge ids per row, edges not placed conflict-free)."""
+        order = np.zeros(max(self.nnz, 1), dtype=np.int32)
+        unplaced = c_i64()
+        _lib.check(self._lib.ldpc_code_schedule(self.handle, c_vp(order.ctypes.data), ctypes.byref(unplaced)),
+                   "ldpc_code_schedule")
+        return order[:self.nnz], unplaced.value
+
     def close(self) -> None:
         if self._h:
             self._lib.ldpc_code_destroy(self._h)

@@ -48,6 +48,7 @@ SIGNATURES = {
                                ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_i64)]),
     "ldpc_code_positions": (c_i32, [c_vp, c_vp, c_vp]),
     "ldpc_code_parity_map": (c_i32, [c_vp, c_vp]),
+    "ldpc_code_schedule": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i64)]),
     "ldpc_code_destroy": (None, [c_vp]),
     "ldpc_encode": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp]),
     "ldpc_syndrome": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),

@@ -21,7 +21,7 @@ int kernel_setup(const void *fn, int threads, size_t smem, int *per_sm) {
         return LDPC_OK;
     }
     size_t &lim = smem_set[std::make_pair(fn, dev)];
-    if (smem > 48 * 1024 && smem > lim) {
+    if (smem > lim) {  // (static shared memory counts against the default 48 KB too)
         LDPC_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         lim = smem;
     }

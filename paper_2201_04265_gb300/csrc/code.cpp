@@ -193,8 +193,9 @@ int upload(T **dst, const T *src, size_t count) {
 }
 
 void free_device(ldpc_code *c) {
-    void *ptrs[] = {c->d.row_ptr, c->d.col_idx,    c->d.col_ptr, c->d.col_edge,
-                    c->d.info_pos, c->d.parity_pos, c->d.AT,      c->d.res_edges};
+    void *ptrs[] = {c->d.row_ptr,   c->d.col_idx,    c->d.col_ptr,  c->d.col_edge,
+                    c->d.info_pos,  c->d.parity_pos, c->d.AT,       c->d.res_edges,
+                    c->d.eval_col,  c->d.eval_edge,  c->d.col_pos};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->d = DeviceCode{};
@@ -212,6 +213,9 @@ int upload_code(ldpc_code *c) {
     LDPC_TRY(upload(&c->d.col_edge, c->col_edge.data(), c->col_edge.size()));
     LDPC_TRY(upload(&c->d.info_pos, c->info_pos.data(), c->info_pos.size()));
     LDPC_TRY(upload(&c->d.parity_pos, c->parity_pos.data(), c->parity_pos.size()));
+    LDPC_TRY(upload(&c->d.eval_col, c->eval_col.data(), c->eval_col.size()));
+    LDPC_TRY(upload(&c->d.eval_edge, c->eval_edge.data(), c->eval_edge.size()));
+    LDPC_TRY(upload(&c->d.col_pos, c->col_pos.data(), c->col_pos.size()));
     std::vector<uint32_t> AT((size_t)c->KW * c->rank);
     for (int32_t j = 0; j < c->rank; ++j)
         for (int32_t w = 0; w < c->KW; ++w) AT[(size_t)w * c->rank + j] = c->A[(size_t)j * c->KW + w];
@@ -295,7 +299,19 @@ int ldpc_code_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t
     c->row_ptr = std::move(rp);
     c->col_idx = std::move(ci);
     int st = build_host(c);
-    if (st == LDPC_OK) st = build_resident_plan(c);
+    if (st == LDPC_OK) st = build_check_schedule(c, resident_group_slots(c));
+    if (st == LDPC_OK) {
+        // derived evaluation-order arrays
+        c->eval_col.resize((size_t)c->nnz);
+        c->pos_of_edge.resize((size_t)c->nnz);
+        for (int64_t p = 0; p < c->nnz; ++p) {
+            c->eval_col[p] = c->col_idx[c->eval_edge[p]];
+            c->pos_of_edge[c->eval_edge[p]] = (int32_t)p;
+        }
+        c->col_pos.resize((size_t)c->nnz);
+        for (int64_t q = 0; q < c->nnz; ++q) c->col_pos[q] = c->pos_of_edge[c->col_edge[q]];
+        st = build_resident_plan(c);
+    }
     if (st == LDPC_OK && !(flags & LDPC_CREATE_HOST_ONLY)) {
         st = upload_code(c);
         if (st != LDPC_OK) free_device(c);
@@ -323,6 +339,13 @@ int ldpc_code_positions(const ldpc_code *c, int32_t *info_pos, int32_t *parity_p
     if (!c) return fail(LDPC_EINVAL, "code is NULL");
     if (info_pos) std::copy(c->info_pos.begin(), c->info_pos.end(), info_pos);
     if (parity_pos) std::copy(c->parity_pos.begin(), c->parity_pos.end(), parity_pos);
+    return LDPC_OK;
+}
+
+int ldpc_code_schedule(const ldpc_code *c, int32_t *eval_edge, int64_t *unplaced) {
+    if (!c) return fail(LDPC_EINVAL, "code is NULL");
+    if (eval_edge) std::copy(c->eval_edge.begin(), c->eval_edge.end(), eval_edge);
+    if (unplaced) *unplaced = c->sched_excess;
     return LDPC_OK;
 }
 

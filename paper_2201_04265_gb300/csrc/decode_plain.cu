@@ -16,7 +16,10 @@
 //   Et[E][Fs]  check messages E_cv       (float or binary16), check-major
 //
 // Only E_cv is stored per edge; the bit-to-check message of Eq. 6 is formed
-// on the fly as L_vc = L_v - E_cv, which is Eq. 6 rearranged.
+// on the fly as L_vc = L_v - E_cv, which is Eq. 6 rearranged.  Edges are
+// stored and combined in the code's evaluation order (the order every
+// decoder shares, from the check schedule), and each bit sums its messages
+// in ascending CSR edge order.
 //
 // Early stop: the check kernel of iteration t also evaluates the syndrome of
 // the hard decisions z^(t-1) = [L^(t-1) >= 0] (it reads every L_v of its
@@ -414,7 +417,7 @@ void launch_check(const ldpc_code *c, const PlainWs &ws, int32_t F, float clip2,
                   int check_syn, uint32_t *unsat, cudaStream_t s) {
     dim3 grid((unsigned)ceil_div(c->m, kCPB), (unsigned)ceil_div(F, kFB * V));
     plain_check<MsgT, DMAX, V><<<grid, kFB, 0, s>>>(ws.Lt, static_cast<MsgT *>(ws.Et), c->d.row_ptr,
-                                                    c->d.col_idx, ws.stop_it, unsat, c->m, F, ws.Fs,
+                                                    c->d.eval_col, ws.stop_it, unsat, c->m, F, ws.Fs,
                                                     clip2, first, check_syn);
 }
 
@@ -423,7 +426,7 @@ void launch_bit(const ldpc_code *c, const PlainWs &ws, int32_t F, int t, int es,
                 const uint32_t *u_cur, uint32_t *u_next, cudaStream_t s) {
     dim3 grid((unsigned)ceil_div(c->n, kVPB), (unsigned)ceil_div(F, kFB * V));
     plain_bit<MsgT, DVMAX, V><<<grid, kFB, 0, s>>>(ws.Rt, ws.Lt, static_cast<const MsgT *>(ws.Et),
-                                                   c->d.col_ptr, c->d.col_edge, ws.stop_it, u_cur,
+                                                   c->d.col_ptr, c->d.col_pos, ws.stop_it, u_cur,
                                                    u_next, c->n, F, ws.Fs, t, es);
 }
 
@@ -454,7 +457,7 @@ int run_plain(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_deco
         } else {
             dim3 grid((unsigned)ceil_div(c->m, kCPB), (unsigned)ceil_div(F, kFB));
             plain_check_wide<MsgT><<<grid, kFB, 0, s>>>(ws.Lt, static_cast<MsgT *>(ws.Et),
-                                                        c->d.row_ptr, c->d.col_idx, ws.stop_it, u_cur,
+                                                        c->d.row_ptr, c->d.eval_col, ws.stop_it, u_cur,
                                                         c->m, F, ws.Fs, clip2, first, check_syn);
         }
         const int e = es ? 1 : 0;
@@ -467,7 +470,7 @@ int run_plain(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_deco
         } else {
             dim3 grid((unsigned)ceil_div(c->n, kVPB), (unsigned)ceil_div(F, kFB));
             plain_bit_wide<MsgT><<<grid, kFB, 0, s>>>(ws.Rt, ws.Lt, static_cast<const MsgT *>(ws.Et),
-                                                      c->d.col_ptr, c->d.col_edge, ws.stop_it, u_cur,
+                                                      c->d.col_ptr, c->d.col_pos, ws.stop_it, u_cur,
                                                       u_next, c->n, F, ws.Fs, t, e);
         }
     }

@@ -7,23 +7,27 @@
 // paper's batch processing (Sec. III-C) mapped onto the GPU: each CTA takes
 // frames from a global work counter and decodes them one group at a time.
 //
-// Per CTA, for a group of G frames (G = 2 with binary16 messages, 1 with FP32
-// messages), shared memory holds
-//   Ls[n]        total LLRs L_v of the G frames      (float2 / float)
-//   Es[n * DV]   check messages E_cv, bit-major: the DV slots of bit v are
-//                Es[v*DV .. v*DV+DV)                 (half2 / float)
-// The G frames of a group share every index computation and every shared
-// memory access (a 4- or 8-byte vector covers both frames).
+// Per CTA (or per team of a CTA, see the mixed-code launch), for a group of
+// G frames (G = 2 with binary16 messages, 1 with FP32 messages), shared
+// memory holds, with P = n rounded up to a power of two:
+//   E[r][P]  check messages, plane r = the r-th edge of each bit (in
+//            ascending CSR edge order); half2 (both frames) or float
+//   L_i[P]   total LLR L_v of frame i (float), one plane per frame
+// All planes have a stride that is a multiple of 32 words, so an access to
+// bit v falls in bank v mod 32.  The check schedule (schedule.cpp) groups the
+// checks of each warp and orders each check's edges so that at every step the
+// 32 lanes touch 32 distinct banks.  An edge is a 16-bit slot s = r P + v:
+// its message is at byte 4 s, its bit's totals at (4 s mod 4P) + plane base.
 //
-// Thread t owns checks t, t+T, ..., and bits t, t+T, ... for the whole
-// kernel: its checks' edge slots (16-bit positions in Es; bit index = slot /
-// DV) are loaded once into registers from a table built at code creation, and
-// its bits' channel LLRs R_v stay in registers while a group is decoded.
+// Thread t owns the checks of its (warp, slot) schedule groups and the bits
+// t, t+T, ...: its checks' slots are loaded once into registers from a table
+// built at code creation, and its bits' channel LLRs stay in registers while
+// a group is decoded.
 //
 // Per iteration: check pass (each thread updates its checks' messages in
 // place and, for early stop, evaluates the syndrome of the previous hard
-// decisions), barrier, bit pass (L_v = R_v + sum of the bit's DV slots, in
-// ascending edge order), barrier.
+// decisions), barrier, bit pass (L_v = R_v + the bit's messages in ascending
+// edge order), barrier.
 #include <algorithm>
 
 #include "check_math.cuh"
@@ -34,6 +38,7 @@ namespace {
 
 constexpr int kResVPT = 16;       // bits per thread
 constexpr int kResMaxThreads = 512;
+constexpr size_t kSmemLimit = 226 * 1024;  // dynamic shared memory per CTA we allow ourselves
 constexpr int kResSlots = 4;      // message slots per bit (column degree <= 4)
 constexpr uint32_t kNoSlot = 0xFFFFu;
 
@@ -43,56 +48,28 @@ struct Shape {
 };
 constexpr Shape kShapes[] = {{6, 8}, {9, 6}, {12, 4}, {16, 3}};
 
-template <int G>
-struct LVec;
-template <>
-struct LVec<1> {
-    using T = float;
-    __device__ static void get(T v, float *x) { x[0] = v; }
-    __device__ static T make(const float *x) { return x[0]; }
-};
-template <>
-struct LVec<2> {
-    using T = float2;
-    __device__ static void get(T v, float *x) {
-        x[0] = v.x;
-        x[1] = v.y;
-    }
-    __device__ static T make(const float *x) { return make_float2(x[0], x[1]); }
-};
-
-// One message slot holding G frames, and the 16-byte record of a bit's slots.
 template <class MsgT, int G>
 struct EVec;
 template <>
 struct EVec<__half, 2> {
     using T = __half2;
-    using Rec = uint4;  // 4 x half2
     __device__ static void get(T v, float *x) {
         const float2 f = __half22float2(v);
         x[0] = f.x;
         x[1] = f.y;
     }
     __device__ static T make(const float *x) { return __floats2half2_rn(x[0], x[1]); }
-    __device__ static void slot(const Rec &r, int q, float *x) {
-        const uint32_t w = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
-        get(*reinterpret_cast<const __half2 *>(&w), x);
-    }
 };
 template <>
 struct EVec<float, 1> {
     using T = float;
-    using Rec = float4;
     __device__ static void get(T v, float *x) { x[0] = v; }
     __device__ static T make(const float *x) { return x[0]; }
-    __device__ static void slot(const Rec &r, int q, float *x) {
-        x[0] = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
-    }
 };
 
 struct ResArgs {
     const float *llr;
-    int32_t F, n, m, NW, T_iters, early_stop;
+    int32_t F, n, npad, m, NW, T_iters, early_stop;
     float clip2;
     const uint32_t *edges;  // [CPT * DCW][T]
     float *post;
@@ -102,20 +79,61 @@ struct ResArgs {
     unsigned *counter;
 };
 
-// Shared-memory layout of a group: Ls[n] (LV::T) then Es[n][4] (EV::T), so
-// that the 16-bit slot s = 4 v + r of an edge gives both addresses:
-// message at byte 4 s * sizeof(slot) / 4, total LLR of bit v = s >> 2.
-template <class MsgT, int G>
-struct Smem {
-    unsigned char *L;  // Ls base
-    unsigned char *E;  // Es base
-    __device__ typename LVec<G>::T &Lv(uint32_t s) const {
-        return *reinterpret_cast<typename LVec<G>::T *>(L + (s >> 2) * sizeof(typename LVec<G>::T));
-    }
-    __device__ typename EVec<MsgT, G>::T &Ev(uint32_t s) const {
-        return *reinterpret_cast<typename EVec<MsgT, G>::T *>(E + s * sizeof(typename EVec<MsgT, G>::T));
-    }
+// 32-bit shared-memory accesses (addresses in the shared window).
+// All shared accesses are volatile asm, so they keep their program order
+// relative to each other and to the barriers; stores also clobber memory.
+__device__ __forceinline__ float lds_f(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_f(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void sts_u(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+template <class T>
+__device__ __forceinline__ uint32_t as_u32(T x) {
+    return *reinterpret_cast<uint32_t *>(&x);
+}
+template <class T>
+__device__ __forceinline__ T from_u32(uint32_t x) {
+    return *reinterpret_cast<T *>(&x);
+}
+
+// Planar shared-memory layout of one frame group (see the file comment):
+// NE message planes, then G planes of totals L, then (regular codes) G planes
+// of channel LLRs R.  Regular codes (three edges per bit) need three message
+// planes and keep R on chip, which frees the registers that would hold it.
+template <bool REG>
+struct Planes {
+    static constexpr int NE = REG ? 3 : kResSlots;
+    static constexpr bool RSM = REG;
 };
+
+template <class MsgT, int G, bool REG>
+struct Smem {
+    uint32_t e0;     // shared address of message plane 0
+    uint32_t l0;     // shared address of the first total plane
+    uint32_t plane;  // bytes per plane, 4 P
+    uint32_t pmask;  // P - 1
+    __device__ uint32_t eaddr(uint32_t s) const { return e0 + 4u * s; }
+    __device__ uint32_t laddr(uint32_t s, int i) const { return l0 + i * plane + 4u * (s & pmask); }
+    __device__ uint32_t eb(int v, int r) const { return e0 + r * plane + 4u * v; }
+    __device__ uint32_t lb(int v, int i) const { return l0 + i * plane + 4u * v; }
+    __device__ uint32_t rb(int v, int i) const { return l0 + (G + i) * plane + 4u * v; }
+};
+
+template <class MsgT, int G, bool REG>
+__host__ __device__ __forceinline__ size_t group_bytes(int npad) {
+    return (size_t)(Planes<REG>::NE + G + (Planes<REG>::RSM ? G : 0)) * 4u * npad;
+}
 
 __device__ __forceinline__ uint32_t slot_of(const uint32_t *w, int j) {
     return (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xFFFFu);
@@ -127,8 +145,7 @@ __device__ __forceinline__ uint32_t slot_of(const uint32_t *w, int j) {
 // hard decisions z = [L >= 0] (L as left by the last bit pass) do not satisfy.
 template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN>
 __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                               const Smem<MsgT, G> &sm, float clip2) {
-    using LV = LVec<G>;
+                                               const Smem<MsgT, G, REG> &sm, float clip2) {
     using EV = EVec<MsgT, G>;
     uint32_t zacc[G];
 #pragma unroll
@@ -149,8 +166,9 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
             if (REG || slot[j] != kNoSlot) {
                 ++d;
                 float L[G], Eo[G];
-                LV::get(sm.Lv(slot[j]), L);
-                EV::get(sm.Ev(slot[j]), Eo);
+#pragma unroll
+                for (int i = 0; i < G; ++i) L[i] = lds_f(sm.laddr(slot[j], i));
+                EV::get(from_u32<typename EV::T>(lds_u(sm.eaddr(slot[j]))), Eo);
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
                     if (SYN) zsgn[i] ^= __float_as_uint(L[i]);  // bit 31: parity of [L < 0]
@@ -196,7 +214,7 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
                                              ((sacc[i] ^ xbits[j][i]) & 0x80000000u));
                     suf[i] = evod_add(suf[i], u[j][i]);
                 }
-                sm.Ev(slot[j]) = EV::make(out);
+                sts_u(sm.eaddr(slot[j]), as_u32(EV::make(out)));
             }
         }
     }
@@ -208,9 +226,9 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
 }
 
 // Syndrome of z = [L >= 0] over the thread's checks (no message update).
-template <class MsgT, int G, int DC, int CPT>
+template <class MsgT, int G, int DC, int CPT, bool REG>
 __device__ __forceinline__ uint32_t syndrome_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                                  const Smem<MsgT, G> &sm) {
+                                                  const Smem<MsgT, G, REG> &sm) {
     uint32_t bad = 0;
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
@@ -219,53 +237,42 @@ __device__ __forceinline__ uint32_t syndrome_pass(const uint32_t (&idx)[CPT][(DC
         for (int j = 0; j < DC; ++j) {
             const uint32_t s = slot_of(idx[k], j);
             if (s == kNoSlot) continue;
-            float L[G];
-            LVec<G>::get(sm.Lv(s), L);
 #pragma unroll
-            for (int i = 0; i < G; ++i) par ^= (uint32_t)(L[i] >= 0.f) << i;
+            for (int i = 0; i < G; ++i) par ^= (uint32_t)(lds_f(sm.laddr(s, i)) >= 0.f) << i;
         }
         bad |= par;  // a check with odd parity is unsatisfied
     }
     return bad;
 }
 
-// Bit pass (Eq. 7): L_v = R_v + the bit's message slots in ascending edge
-// order; frames not in `active` keep their L_v.  REG codes have exactly three
-// edges per bit; otherwise all four slots are summed (unused ones hold 0).
-template <class MsgT, int G, bool REG, bool SYN>
-__device__ __forceinline__ void bit_pass(const float (&R)[kResVPT][G], const Smem<MsgT, G> &sm,
-                                         int n, int tid, int T, uint32_t active, uint32_t exists) {
-    using LV = LVec<G>;
+// Bit pass (Eq. 7): L_v = R_v + the bit's messages in ascending edge order;
+// frames not in `active` keep their L_v.  REG codes have exactly three edges
+// per bit and R on chip; otherwise all four planes are summed (unused slots
+// hold 0) and R comes from registers.
+template <class MsgT, int G, bool REG, bool SYN, int NR>
+__device__ __forceinline__ void bit_pass(const float (&R)[NR][G], const Smem<MsgT, G, REG> &sm, int n,
+                                         int tid, int T, uint32_t active) {
     using EV = EVec<MsgT, G>;
-    constexpr int NS = REG ? 3 : kResSlots;
+    constexpr int NS = Planes<REG>::NE;
 #pragma unroll
     for (int k = 0; k < kResVPT; ++k) {
         const int v = tid + k * T;
         if (v < n) {
-            const typename EV::Rec rec =
-                *reinterpret_cast<const typename EV::Rec *>(sm.E + (size_t)v * kResSlots * sizeof(typename EV::T));
             float L[G];
 #pragma unroll
-            for (int i = 0; i < G; ++i) L[i] = R[k][i];
+            for (int i = 0; i < G; ++i) L[i] = REG ? lds_f(sm.rb(v, i)) : R[REG ? 0 : k][i];
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 float e[G];
-                EV::slot(rec, q, e);
+                EV::get(from_u32<typename EV::T>(lds_u(sm.eb(v, q))), e);
 #pragma unroll
                 for (int i = 0; i < G; ++i) L[i] += e[i];
             }
-            if (SYN)
 #pragma unroll
-                for (int i = 0; i < G; ++i) L[i] += 0.f;  // no -0: z = [L >= 0] by sign
-            typename LV::T *dst = reinterpret_cast<typename LV::T *>(sm.L) + v;
-            if (active != exists) {
-                float old[G];
-                LV::get(*dst, old);
-#pragma unroll
-                for (int i = 0; i < G; ++i)
-                    if (!((active >> i) & 1u)) L[i] = old[i];
+            for (int i = 0; i < G; ++i) {
+                if (SYN) L[i] += 0.f;  // no -0: z = [L >= 0] by sign
+                if ((active >> i) & 1u) sts_f(sm.lb(v, i), L[i]);
             }
-            *dst = LV::make(L);
         }
     }
 }
@@ -303,45 +310,52 @@ struct SubTeam {
     }
 };
 
-// Where the G frames of a group come from and go to (NULL llr = no frame).
+// Where the G frames of a group come from and go to (null llr = no frame).
 template <int G>
-struct FrameIO {
-    const float *llr[G];
-    float *post[G];
-    uint32_t *hard[G];
-    int32_t *iters[G];
-    uint8_t *ok[G];
+struct ResIO {
+    const float *llr_[G];
+    float *post_[G];
+    uint32_t *hard_[G];
+    int32_t *iters_[G];
+    uint8_t *ok_[G];
+    __device__ bool exists(int i) const { return llr_[i] != nullptr; }
+    __device__ const float *llr(int i) const { return llr_[i]; }
+    __device__ float *post(int i) const { return post_[i]; }
+    __device__ uint32_t *hard(int i) const { return hard_[i]; }
+    __device__ int32_t *iters(int i) const { return iters_[i]; }
+    __device__ uint8_t *ok(int i) const { return ok_[i]; }
 };
 
 // Decodes one group of G frames with the team's threads: load R, iterate
 // (check pass, bit pass), final syndrome, outputs.  Ends with a team barrier.
-template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, class Team>
+template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, class Team, class IO>
 __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                             const Smem<MsgT, G> &sm, int n, const FrameIO<G> &io,
-                                             int T_iters, float clip2) {
-    using LV = LVec<G>;
-    using EV = EVec<MsgT, G>;
+                                             const Smem<MsgT, G, REG> &sm, int n, int npad,
+                                             const IO &io, int T_iters, float clip2) {
     const int tid = tm.tid(), T = tm.size();
     const int lane = threadIdx.x & 31;
     uint32_t exists = 0;
 #pragma unroll
-    for (int i = 0; i < G; ++i) exists |= (uint32_t)(io.llr[i] != nullptr) << i;
+    for (int i = 0; i < G; ++i) exists |= (uint32_t)io.exists(i) << i;
 
-    // channel LLRs (log2 units) into registers and L_v = R_v; messages 0
-    float R[kResVPT][G];
+    // channel LLRs (log2 units) into shared memory (REG) or registers, and
+    // L_v = R_v; messages 0
+    constexpr int NR = REG ? 1 : kResVPT;
+    float R[NR][G];
 #pragma unroll
     for (int k = 0; k < kResVPT; ++k) {
         const int v = tid + k * T;
 #pragma unroll
-        for (int i = 0; i < G; ++i) R[k][i] = (v < n && io.llr[i]) ? io.llr[i][v] * kLog2e : 0.f;
-        if (v < n) {
-            reinterpret_cast<typename LV::T *>(sm.L)[v] = LV::make(R[k]);
-            *reinterpret_cast<uint4 *>(sm.E + (size_t)v * kResSlots * sizeof(typename EV::T)) =
-                make_uint4(0u, 0u, 0u, 0u);
-            if (sizeof(typename EV::T) == 8)
-                *reinterpret_cast<uint4 *>(sm.E + (size_t)v * kResSlots * 8 + 16) = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = 0; i < G; ++i) {
+            const float r = (v < n && ((exists >> i) & 1u)) ? io.llr(i)[v] * kLog2e : 0.f;
+            if (!REG) R[REG ? 0 : k][i] = r;
+            if (v < n) {
+                sts_f(sm.lb(v, i), r);
+                if (REG) sts_f(sm.rb(v, i), r);
+            }
         }
     }
+    for (int w = tid; w < Planes<REG>::NE * npad; w += T) sts_u(sm.e0 + 4u * w, 0u);
     tm.sync();
 
     uint32_t active = exists, okm = 0;
@@ -365,11 +379,11 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
             check_pass<MsgT, G, DC, CPT, REG, false>(idx, sm, clip2);
             tm.sync();
         }
-        bit_pass<MsgT, G, REG, SYN>(R, sm, n, tid, T, active, exists);
+        bit_pass<MsgT, G, REG, SYN>(R, sm, n, tid, T, active);
         tm.sync();
     }
     if (active) {  // frames that ran every iteration: syndrome of the final z
-        const uint32_t bad = syndrome_pass<MsgT, G, DC, CPT>(idx, sm);
+        const uint32_t bad = syndrome_pass<MsgT, G, DC, CPT, REG>(idx, sm);
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             const int any_bad = tm.any((int)((bad >> i) & 1u));
@@ -384,37 +398,35 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
     for (int k = 0; k < kResVPT; ++k) {
         const int v = tid + k * T;
         const int v0 = v - lane;
-        float L[G];
-        if (v < n) {
-            LV::get(reinterpret_cast<typename LV::T *>(sm.L)[v], L);
-        } else {
-#pragma unroll
-            for (int i = 0; i < G; ++i) L[i] = 0.f;
-        }
 #pragma unroll
         for (int i = 0; i < G; ++i) {
-            const uint32_t word = __ballot_sync(0xffffffffu, v < n && L[i] >= 0.f);
-            if (io.llr[i]) {
-                if (io.post[i] && v < n) io.post[i][v] = T_iters == 0 ? io.llr[i][v] : L[i] * kLn2;
-                if (io.hard[i] && lane == 0 && v0 < n) io.hard[i][v0 >> 5] = word;
+            const float L = v < n ? lds_f(sm.lb(v, i)) : 0.f;
+            const uint32_t word = __ballot_sync(0xffffffffu, v < n && L >= 0.f);
+            if ((exists >> i) & 1u) {
+                float *post = io.post(i);
+                uint32_t *hard = io.hard(i);
+                if (post && v < n) post[v] = T_iters == 0 ? io.llr(i)[v] : L * kLn2;
+                if (hard && lane == 0 && v0 < n) hard[v0 >> 5] = word;
             }
         }
     }
     if (tid == 0)
 #pragma unroll
         for (int i = 0; i < G; ++i)
-            if (io.llr[i]) {
-                if (io.iters[i]) *io.iters[i] = it_done[i];
-                if (io.ok[i]) *io.ok[i] = (uint8_t)((okm >> i) & 1u);
+            if ((exists >> i) & 1u) {
+                if (int32_t *it = io.iters(i)) *it = it_done[i];
+                if (uint8_t *okp = io.ok(i)) *okp = (uint8_t)((okm >> i) & 1u);
             }
     tm.sync();
 }
 
-template <class MsgT, int G>
-__device__ __forceinline__ Smem<MsgT, G> smem_at(unsigned char *base, int n) {
-    Smem<MsgT, G> sm;
-    sm.L = base;
-    sm.E = base + (((size_t)n * sizeof(typename LVec<G>::T) + 15) & ~size_t(15));
+template <class MsgT, int G, bool REG>
+__device__ __forceinline__ Smem<MsgT, G, REG> smem_at(unsigned char *base, int npad) {
+    Smem<MsgT, G, REG> sm;
+    sm.e0 = (uint32_t)__cvta_generic_to_shared(base);
+    sm.plane = 4u * (uint32_t)npad;
+    sm.pmask = (uint32_t)npad - 1u;
+    sm.l0 = sm.e0 + Planes<REG>::NE * sm.plane;
     return sm;
 }
 
@@ -423,7 +435,7 @@ __global__ void __launch_bounds__(kResMaxThreads)
 resident_kernel(ResArgs a) {
     constexpr int DCW = (DC + 1) / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem<MsgT, G> sm = smem_at<MsgT, G>(smem_raw, a.n);
+    const Smem<MsgT, G, REG> sm = smem_at<MsgT, G, REG>(smem_raw, a.npad);
     __shared__ int s_group;
     const int T = blockDim.x, tid = threadIdx.x;
     uint32_t idx[CPT][DCW];
@@ -438,18 +450,18 @@ resident_kernel(ResArgs a) {
         const int grp = s_group;
         __syncthreads();
         if (grp >= groups) break;
-        FrameIO<G> io;
+        ResIO<G> io;
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             const int64_t f = (int64_t)grp * G + i;
             const bool ex = f < a.F;
-            io.llr[i] = ex ? a.llr + f * a.n : nullptr;
-            io.post[i] = ex && a.post ? a.post + f * a.n : nullptr;
-            io.hard[i] = ex && a.hard ? a.hard + f * a.NW : nullptr;
-            io.iters[i] = ex && a.iters ? a.iters + f : nullptr;
-            io.ok[i] = ex && a.ok ? a.ok + f : nullptr;
+            io.llr_[i] = ex ? a.llr + f * a.n : nullptr;
+            io.post_[i] = ex && a.post ? a.post + f * a.n : nullptr;
+            io.hard_[i] = ex && a.hard ? a.hard + f * a.NW : nullptr;
+            io.iters_[i] = ex && a.iters ? a.iters + f : nullptr;
+            io.ok_[i] = ex && a.ok ? a.ok + f : nullptr;
         }
-        decode_group<MsgT, G, DC, CPT, REG, SYN>(BlockTeam{}, idx, sm, a.n, io, a.T_iters, a.clip2);
+        decode_group<MsgT, G, DC, CPT, REG, SYN>(BlockTeam{}, idx, sm, a.n, a.npad, io, a.T_iters, a.clip2);
     }
 }
 
@@ -472,49 +484,82 @@ KernelFn pick_kernel(int dc, bool reg, bool syn) {
     }
 }
 
-size_t res_smem(const ldpc_code *c, bool fp16) {
-    const int G = fp16 ? 2 : 1;
-    const size_t lbytes = ((size_t)c->n * 4 * G + 15) & ~size_t(15);
-    return lbytes + (size_t)c->n * kResSlots * (fp16 ? 2 : 4) * G;
+int pad_bits(const ldpc_code *c) {
+    int p = 32;
+    while (p < c->n) p *= 2;
+    return p;
 }
 
-// Edge-slot table for threads of a team of T: [CPT * DCW][T] 32-bit words,
-// two 16-bit slots each; check t + k T goes to thread t, slot k.  The slot of
-// an edge is 4 v + r, v its bit and r its rank in v's column.
+size_t res_smem(const ldpc_code *c, bool fp16, bool reg) {
+    const int P = pad_bits(c);
+    if (reg) return fp16 ? group_bytes<__half, 2, true>(P) : group_bytes<float, 1, true>(P);
+    return fp16 ? group_bytes<__half, 2, false>(P) : group_bytes<float, 1, false>(P);
+}
+
+// Edge-slot table for a team of T threads: [CPT * DCW][T] 32-bit words, two
+// 16-bit slots each.  Warp group g of the check schedule goes to warp
+// g mod (T/32), check slot g / (T/32); lane u takes the group's u-th check,
+// whose slots are listed in evaluation order.  The slot of an edge is r P + v,
+// v its bit and r the edge's rank in v's column (ascending CSR edge order).
+// Returns an empty table if the schedule needs more slots than CPT.
 std::vector<uint32_t> build_slot_table(const ldpc_code *c, int dc, int cpt, int T) {
     const int DCW = (dc + 1) / 2;
-    std::vector<uint32_t> slot_of((size_t)c->nnz);
+    const int npad = pad_bits(c);
+    const int warps = T / 32;
+    std::vector<uint32_t> rank((size_t)c->nnz);
     for (int32_t v = 0; v < c->n; ++v)
         for (int32_t q = c->col_ptr[v]; q < c->col_ptr[v + 1]; ++q)
-            slot_of[c->col_edge[q]] = (uint32_t)(v * kResSlots + (q - c->col_ptr[v]));
+            rank[c->col_edge[q]] = (uint32_t)(q - c->col_ptr[v]);
     std::vector<uint32_t> tab((size_t)cpt * DCW * T, 0xFFFFFFFFu);
-    for (int t = 0; t < T; ++t)
-        for (int k = 0; k < cpt; ++k) {
-            const int64_t cidx = t + (int64_t)k * T;
-            if (cidx >= c->m) continue;
-            const int32_t e0 = c->row_ptr[cidx], d = c->row_ptr[cidx + 1] - e0;
+    const int ngroups = (int)(c->sched_groups.size() / 32);
+    for (int g = 0; g < ngroups; ++g) {
+        const int w = g % warps, k = g / warps;
+        if (k >= cpt) return {};
+        for (int u = 0; u < 32; ++u) {
+            const int32_t chk = c->sched_groups[(size_t)g * 32 + u];
+            if (chk < 0) continue;
+            const int t = 32 * w + u;
+            const int32_t e0 = c->row_ptr[chk], d = c->row_ptr[chk + 1] - e0;
             for (int j = 0; j < d; ++j) {
-                uint32_t &w = tab[(size_t)(k * DCW + j / 2) * T + t];
+                const int32_t e = c->eval_edge[e0 + j];
+                const uint32_t slot = rank[e] * (uint32_t)npad + (uint32_t)c->col_idx[e];
+                uint32_t &word = tab[(size_t)(k * DCW + j / 2) * T + t];
                 const int sh = (j & 1) * 16;
-                w = (w & ~(0xFFFFu << sh)) | (slot_of[e0 + j] << sh);
+                word = (word & ~(0xFFFFu << sh)) | (slot << sh);
             }
         }
+    }
     return tab;
 }
 
 const Shape *pick_shape(const ldpc_code *c) {
-    if (c->dv_max > kResSlots || (int64_t)c->n * kResSlots > 0xFFFE) return nullptr;
+    // slots up to (slots - 1) P + n - 1 must stay below the 16-bit empty mark
+    if (c->dv_max > kResSlots || (int64_t)(kResSlots - 1) * pad_bits(c) + c->n > 0xFFFE) return nullptr;
     for (const Shape &s : kShapes)
         if (s.dc >= c->dc_max) return &s;
     return nullptr;
 }
 
+// Threads per frame group: enough for the bits (kResVPT each) and for the
+// checks with about 5 % spare check slots, which the check schedule uses to
+// balance banks.
 int team_threads(const ldpc_code *c, const Shape &s) {
-    const int64_t need = std::max(ceil_div(c->m, s.cpt), ceil_div(c->n, kResVPT));
-    return (int)ceil_div(need, 32) * 32;
+    const int64_t need = std::max(ceil_div(c->m + c->m / 20 + 1, s.cpt), ceil_div(c->n, kResVPT));
+    return (int)std::min<int64_t>(ceil_div(need, 32) * 32,
+                                  std::max<int64_t>(kResMaxThreads, ceil_div(ceil_div(c->m, s.cpt), 32) * 32));
 }
 
 }  // namespace
+
+// Warp groups the single-code resident launch offers (0 without a resident
+// layout): the check schedule spreads the checks over all of them.
+int resident_group_slots(const ldpc_code *c) {
+    const Shape *shape = pick_shape(c);
+    if (!shape) return 0;
+    const int T = team_threads(c, *shape);
+    if (T > kResMaxThreads) return 0;
+    return (T / 32) * shape->cpt;
+}
 
 // Host-side plan of the single-code resident launch: row shape, thread count
 // and slot table.
@@ -526,6 +571,7 @@ int build_resident_plan(ldpc_code *c) {
     const int T = team_threads(c, *shape);
     if (T > kResMaxThreads) return LDPC_OK;
     p.edges = build_slot_table(c, shape->dc, shape->cpt, T);
+    if (p.edges.empty()) return LDPC_OK;
     p.dc_pad = shape->dc;
     p.dv_pad = kResSlots;
     p.rows_pad = T;  // thread count of the launch
@@ -537,7 +583,7 @@ int build_resident_plan(ldpc_code *c) {
 
 bool resident_fits(const ldpc_code *c, const ldpc_decode_opts *o) {
     if (!c->res.ok) return false;
-    return res_smem(c, o->msg_fp16 != 0) <= 220 * 1024;
+    return res_smem(c, o->msg_fp16 != 0, c->res.regular) <= kSmemLimit;
 }
 
 size_t resident_workspace(const ldpc_code *, int32_t, const ldpc_decode_opts *) { return 256; }
@@ -552,7 +598,7 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
                        : pick_kernel<float, 1>(c->res.dc_pad, c->res.regular, syn);
     if (!fn) return fail(LDPC_ENOTSUP, "no resident kernel for row degree %d", c->res.dc_pad);
     const int T = c->res.rows_pad;
-    const size_t smem = res_smem(c, fp16);
+    const size_t smem = res_smem(c, fp16, c->res.regular);
     int sms = 0, per_sm = 0;
     LDPC_TRY(sm_count(&sms));
     LDPC_TRY(kernel_setup((const void *)fn, T, smem, &per_sm));
@@ -564,6 +610,7 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
     a.llr = d_llr;
     a.F = F;
     a.n = c->n;
+    a.npad = pad_bits(c);
     a.m = c->m;
     a.NW = c->NW;
     a.T_iters = o->max_iters;
@@ -603,7 +650,7 @@ namespace {
 constexpr int kMixThreads = 512;
 
 struct MixedDesc {
-    int32_t n, dc, team, teams, code;
+    int32_t n, npad, dc, team, teams, code;
     const uint32_t *edges;  // [cpt * DCW][team]
 };
 
@@ -624,11 +671,6 @@ struct MixedArgs {
     int32_t T_iters, gpi;
     float clip2;
 };
-
-template <class MsgT, int G>
-__host__ __device__ __forceinline__ size_t team_bytes(int n) {
-    return (((size_t)n * sizeof(float) * G + 15) & ~size_t(15)) + (size_t)n * kResSlots * sizeof(MsgT) * G;
-}
 
 __global__ void mixed_count(const int32_t *__restrict__ frame_code, int32_t F, int32_t ncodes,
                             unsigned *__restrict__ count, int32_t *__restrict__ iters,
@@ -672,8 +714,25 @@ __global__ void mixed_scatter(const int32_t *__restrict__ frame_code, int32_t F,
     sorted[start[c] + atomicAdd(&fill[c], 1u)] = (int32_t)f;
 }
 
+// Not inlined: each row shape gets its own register allocation instead of
+// the union of all three inside one kernel body.
+template <int G>
+struct MixIO {
+    const MixedArgs &a;
+    unsigned first, cnt, st;  // group's first index in the code's bucket
+    __device__ bool exists(int i) const { return first + i < cnt; }
+    __device__ int f(int i) const { return a.sorted[st + first + i]; }
+    __device__ const float *llr(int i) const { return a.llr + a.llr_off[f(i)]; }
+    __device__ float *post(int i) const { return a.post ? a.post + a.llr_off[f(i)] : nullptr; }
+    __device__ uint32_t *hard(int i) const { return a.hard ? a.hard + a.hard_off[f(i)] : nullptr; }
+    __device__ int32_t *iters(int i) const { return a.iters ? a.iters + f(i) : nullptr; }
+    __device__ uint8_t *ok(int i) const { return a.ok ? a.ok + f(i) : nullptr; }
+};
+
+// Not inlined: each row shape gets its own register allocation instead of
+// sharing one with the other two shapes in the kernel body.
 template <class MsgT, int G, int DC, int CPT, bool SYN>
-__device__ __forceinline__ void mixed_run(const SubTeam &tm, const MixedDesc &d, const MixedArgs &a,
+__device__ __noinline__ void mixed_run(const SubTeam &tm, const MixedDesc &d, const MixedArgs &a,
                                           unsigned char *base, unsigned local) {
     constexpr int DCW = (DC + 1) / 2;
     uint32_t idx[CPT][DCW];
@@ -681,32 +740,14 @@ __device__ __forceinline__ void mixed_run(const SubTeam &tm, const MixedDesc &d,
     for (int k = 0; k < CPT; ++k)
 #pragma unroll
         for (int w = 0; w < DCW; ++w) idx[k][w] = __ldg(&d.edges[(size_t)(k * DCW + w) * d.team + tm.tid()]);
-    const Smem<MsgT, G> sm = smem_at<MsgT, G>(base, d.n);
+    const Smem<MsgT, G, true> sm = smem_at<MsgT, G, true>(base, d.npad);
     const unsigned cnt = a.count[d.code], st = a.start[d.code];
     const int team = tm.base / d.team;
     for (int gi = 0; gi < a.gpi; ++gi) {
         const unsigned grp = (local * a.gpi + gi) * d.teams + team;
         if ((size_t)grp * G >= cnt) break;
-        FrameIO<G> io;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const unsigned j = grp * G + i;
-            if (j < cnt) {
-                const int f = a.sorted[st + j];
-                io.llr[i] = a.llr + a.llr_off[f];
-                io.post[i] = a.post ? a.post + a.llr_off[f] : nullptr;
-                io.hard[i] = a.hard ? a.hard + a.hard_off[f] : nullptr;
-                io.iters[i] = a.iters ? a.iters + f : nullptr;
-                io.ok[i] = a.ok ? a.ok + f : nullptr;
-            } else {
-                io.llr[i] = nullptr;
-                io.post[i] = nullptr;
-                io.hard[i] = nullptr;
-                io.iters[i] = nullptr;
-                io.ok[i] = nullptr;
-            }
-        }
-        decode_group<MsgT, G, DC, CPT, true, SYN>(tm, idx, sm, d.n, io, a.T_iters, a.clip2);
+        const MixIO<G> io{a, grp * G, cnt, st};
+        decode_group<MsgT, G, DC, CPT, true, SYN>(tm, idx, sm, d.n, d.npad, io, a.T_iters, a.clip2);
     }
 }
 
@@ -728,7 +769,7 @@ mixed_kernel(MixedArgs a) {
         const int team = threadIdx.x / d.team;
         if (team < d.teams) {
             const SubTeam tm{team * d.team, d.team, 1 + team};
-            unsigned char *base = smem_raw + (size_t)team * team_bytes<MsgT, G>(d.n);
+            unsigned char *base = smem_raw + (size_t)team * group_bytes<MsgT, G, true>(d.npad);
             const unsigned local = item - a.item_off[p];
             switch (d.dc) {
                 case 6: mixed_run<MsgT, G, 6, 8, SYN>(tm, d, a, base, local); break;
@@ -842,10 +883,11 @@ int ldpc_mixed_create(const ldpc_code *const *codes, int32_t ncodes, int32_t msg
         int team = 32;
         while (team < team_threads(c, *sh)) team *= 2;
         if (team > kMixThreads) return cleanup(fail(LDPC_ENOTSUP, "code %d is too long for a mixed batch", i));
-        const size_t tb = G == 2 ? team_bytes<__half, 2>(c->n) : team_bytes<float, 1>(c->n);
-        const int teams = std::min<int>(kMixThreads / team, (int)((220 * 1024) / tb));
+        const size_t tb = res_smem(c, G == 2, true);
+        const int teams = std::min<int>(kMixThreads / team, (int)(kSmemLimit / tb));
         if (teams < 1) return cleanup(fail(LDPC_ENOTSUP, "code %d does not fit in shared memory", i));
         std::vector<uint32_t> tab = build_slot_table(c, sh->dc, sh->cpt, team);
+        if (tab.empty()) return cleanup(fail(LDPC_ENOTSUP, "code %d: no slot table for team %d", i, team));
         uint32_t *dt = nullptr;
         cudaError_t err = cudaMalloc(&dt, sizeof(uint32_t) * tab.size());
         if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMalloc(mixed slot table)"));
@@ -853,7 +895,7 @@ int ldpc_mixed_create(const ldpc_code *const *codes, int32_t ncodes, int32_t msg
         err = cudaMemcpy(dt, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice);
         if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMemcpy(mixed slot table)"));
         p->codes.push_back(c);
-        p->host_desc.push_back(MixedDesc{c->n, sh->dc, team, teams, i, dt});
+        p->host_desc.push_back(MixedDesc{c->n, pad_bits(c), sh->dc, team, teams, i, dt});
         p->smem = std::max(p->smem, (size_t)teams * tb);
     }
     cudaError_t err = cudaMalloc(&p->d_desc, sizeof(MixedDesc) * ncodes);

@@ -41,9 +41,12 @@ struct DeviceCode {
     int32_t *col_edge = nullptr;   // [E]  bit-major list of edge ids (ascending)
     int32_t *info_pos = nullptr;   // [k]
     int32_t *parity_pos = nullptr; // [rank]
-    uint32_t *AT = nullptr;        // [KW][rank] parity map, word-major
+    int32_t *eval_col = nullptr;  // [E]  column at each evaluation position
+    int32_t *eval_edge = nullptr; // [E]  CSR edge id at each evaluation position
+    int32_t *col_pos = nullptr;   // [E]  evaluation position of col_edge[q]
+    uint32_t *AT = nullptr;       // [KW][rank] parity map, word-major
     // resident decoder tables (see decode_resident.cu)
-    uint32_t *res_edges = nullptr; // per check-slot packed (bit index, slot) records
+    uint32_t *res_edges = nullptr; // resident slot table of the single-code launch
     int32_t res_edges_len = 0;
 };
 
@@ -67,6 +70,12 @@ struct ldpc_code {
     int32_t dc_max = 0, dv_max = 0, dc_min = 0, dv_min = 0;
     std::vector<int32_t> row_ptr, col_idx, col_ptr, col_edge, info_pos, parity_pos;
     std::vector<uint32_t> A;  // [rank][KW]
+    // check evaluation order (shared by every decoder; see schedule.cpp):
+    // positions row_ptr[c]..row_ptr[c+1]-1 hold check c's edges in the order
+    // its inputs are combined
+    std::vector<int32_t> eval_edge, eval_col, col_pos, pos_of_edge;
+    std::vector<int32_t> sched_groups;  // [ceil(m/32)][32] checks per warp group, -1 = none
+    int64_t sched_excess = 0;           // edges above d_c per (group, bank): 0 = conflict-free
     bool on_device = false;
     int device = -1;
     ldpc::DeviceCode d;
@@ -74,6 +83,8 @@ struct ldpc_code {
 };
 
 namespace ldpc {
+int build_check_schedule(ldpc_code *c, int ngroups);  // schedule.cpp
+int resident_group_slots(const ldpc_code *c);       // decode_resident.cu
 // Sets a kernel's dynamic shared-memory limit (once per kernel and device)
 // and returns its resident CTAs per SM for the launch shape (cached), so that
 // launchers make no attribute calls on the repeat calls a CUDA graph captures.

@@ -23,7 +23,8 @@
 // Units: as in the decoders, LLRs are held in log2 units; this Jacobian is
 // unit-free and the weight gradient equals that in natural units.
 //
-// Layout: frame-interleaved [index][Fs] as in the plain decoder.  The weight
+// Layout: frame-interleaved [index][Fs] as in the plain decoder; messages at
+// the code's evaluation positions, weights and weight gradients by CSR edge.  The weight
 // gradient is reduced over frames deterministically (warp shuffles, then the
 // warps of a block in order, then the frame blocks in order).
 #include <algorithm>
@@ -137,8 +138,8 @@ template <int DMAX>
 __global__ void __launch_bounds__(kWFB)
 wbp_check(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
           const float *__restrict__ wprev, float *__restrict__ Ecur,
-          const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx, int32_t m,
-          int32_t F, int64_t Fs, float clip2) {
+          const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ eval_col,
+          const int32_t *__restrict__ eval_edge, int32_t m, int32_t F, int64_t Fs, float clip2) {
     const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
     const int c = blockIdx.x;
     if (f >= F || c >= m) return;
@@ -149,9 +150,9 @@ wbp_check(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
         if (j < d) {
-            const int e = e0 + j;
-            const float L = Lprev[(int64_t)__ldg(&col_idx[e]) * Fs + f];
-            const float x = Eprev ? fmaf(-__ldg(&wprev[e]), Eprev[(int64_t)e * Fs + f], L) : L;
+            const int e = e0 + j;  // evaluation position
+            const float L = Lprev[(int64_t)__ldg(&eval_col[e]) * Fs + f];
+            const float x = Eprev ? fmaf(-__ldg(&wprev[__ldg(&eval_edge[e])]), Eprev[(int64_t)e * Fs + f], L) : L;
             xb[j] = __float_as_uint(x);
             sacc ^= xb[j];
             u[j] = check_u(fminf(fmaxf(x, -clip2), clip2));
@@ -178,15 +179,14 @@ wbp_check(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
 __global__ void __launch_bounds__(kWFB)
 wbp_bit(const float *__restrict__ Rt, const float *__restrict__ Ecur, const float *__restrict__ wcur,
         float *__restrict__ Lcur, const int32_t *__restrict__ col_ptr,
-        const int32_t *__restrict__ col_edge, int32_t n, int32_t F, int64_t Fs) {
+        const int32_t *__restrict__ col_edge, const int32_t *__restrict__ col_pos, int32_t n,
+        int32_t F, int64_t Fs) {
     const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
     const int v = blockIdx.x;
     if (f >= F || v >= n) return;
     float L = Rt[(int64_t)v * Fs + f];
-    for (int q = __ldg(&col_ptr[v]), q1 = __ldg(&col_ptr[v + 1]); q < q1; ++q) {
-        const int e = __ldg(&col_edge[q]);
-        L = fmaf(__ldg(&wcur[e]), Ecur[(int64_t)e * Fs + f], L);
-    }
+    for (int q = __ldg(&col_ptr[v]), q1 = __ldg(&col_ptr[v + 1]); q < q1; ++q)
+        L = fmaf(__ldg(&wcur[__ldg(&col_edge[q])]), Ecur[(int64_t)__ldg(&col_pos[q]) * Fs + f], L);
     Lcur[(int64_t)v * Fs + f] = L;
 }
 
@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(kWFB)
 wbp_bit_back(const float *__restrict__ gout2, const float *__restrict__ gX,
              const float *__restrict__ Ecur, const float *__restrict__ wcur, float *__restrict__ gE,
              float *__restrict__ gR, float *__restrict__ gwpart, const int32_t *__restrict__ col_ptr,
-             const int32_t *__restrict__ col_edge, int32_t n, int32_t F, int64_t Fs, int last,
-             int first_acc, int32_t nnz) {
+             const int32_t *__restrict__ col_edge, const int32_t *__restrict__ col_pos, int32_t n,
+             int32_t F, int64_t Fs, int last, int first_acc, int32_t nnz) {
     __shared__ float red[kWFB / 32];
     const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
     const int v = blockIdx.x;
@@ -216,17 +216,17 @@ wbp_bit_back(const float *__restrict__ gout2, const float *__restrict__ gX,
         if (last) {
             gL = gout2[(int64_t)v * Fs + f];
         } else {
-            for (int q = q0; q < q1; ++q) gL += gX[(int64_t)__ldg(&col_edge[q]) * Fs + f];
+            for (int q = q0; q < q1; ++q) gL += gX[(int64_t)__ldg(&col_pos[q]) * Fs + f];
         }
         const int64_t iv = (int64_t)v * Fs + f;
         gR[iv] = first_acc ? gL : gR[iv] + gL;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = q0; q < q1; ++q) {
-        const int e = __ldg(&col_edge[q]);
+        const int e = __ldg(&col_edge[q]);  // CSR edge: weight and gradient index
         float contrib = 0.f;
         if (live) {
-            const int64_t ie = (int64_t)e * Fs + f;
+            const int64_t ie = (int64_t)__ldg(&col_pos[q]) * Fs + f;
             const float g = last ? gL : gL - gX[ie];
             gE[ie] = __ldg(&wcur[e]) * g;
             contrib = Ecur[ie] * g;
@@ -251,7 +251,8 @@ __global__ void __launch_bounds__(kWFB)
 wbp_check_back(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
                const float *__restrict__ wprev, const float *__restrict__ gE,
                float *__restrict__ gX, const int32_t *__restrict__ row_ptr,
-               const int32_t *__restrict__ col_idx, int32_t m, int32_t F, int64_t Fs, float clip2) {
+               const int32_t *__restrict__ eval_col, const int32_t *__restrict__ eval_edge, int32_t m,
+               int32_t F, int64_t Fs, float clip2) {
     const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
     const int c = blockIdx.x;
     if (f >= F || c >= m) return;
@@ -262,9 +263,9 @@ wbp_check_back(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
         if (j < d) {
-            const int e = e0 + j;
-            const float L = Lprev[(int64_t)__ldg(&col_idx[e]) * Fs + f];
-            const float x = Eprev ? fmaf(-__ldg(&wprev[e]), Eprev[(int64_t)e * Fs + f], L) : L;
+            const int e = e0 + j;  // evaluation position
+            const float L = Lprev[(int64_t)__ldg(&eval_col[e]) * Fs + f];
+            const float x = Eprev ? fmaf(-__ldg(&wprev[__ldg(&eval_edge[e])]), Eprev[(int64_t)e * Fs + f], L) : L;
             sgn |= (__float_as_uint(x) >> 31) << j;
             inmask |= (uint32_t)(fabsf(x) <= clip2) << j;
             const float y = fminf(fabsf(x), clip2);
@@ -312,14 +313,14 @@ wbp_check_back(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
 
 // gR_v += sum_e gx^1_e (x^1 = R).
 __global__ void wbp_final_r(const float *__restrict__ gX, float *__restrict__ gR,
-                            const int32_t *__restrict__ col_ptr, const int32_t *__restrict__ col_edge,
+                            const int32_t *__restrict__ col_ptr, const int32_t *__restrict__ col_pos,
                             int32_t n, int32_t F, int64_t Fs) {
     const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
     const int v = blockIdx.x;
     if (f >= F || v >= n) return;
     float s = gR[(int64_t)v * Fs + f];
     for (int q = __ldg(&col_ptr[v]), q1 = __ldg(&col_ptr[v + 1]); q < q1; ++q)
-        s += gX[(int64_t)__ldg(&col_edge[q]) * Fs + f];
+        s += gX[(int64_t)__ldg(&col_pos[q]) * Fs + f];
     gR[(int64_t)v * Fs + f] = s;
 }
 
@@ -377,11 +378,11 @@ int ldpc_wbp_forward(const ldpc_code *c, const float *d_llr, int32_t F, int32_t 
         float *Ecur = ck.E + (t - 1) * eF;
         float *Lcur = ck.L + (t - 1) * nF;
         const dim3 cg((unsigned)c->m, (unsigned)ceil_div(F, kWFB));
-        wbp_check<kWMaxDeg><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, Ecur, c->d.row_ptr, c->d.col_idx,
-                                                c->m, F, ck.Fs, clip2);
+        wbp_check<kWMaxDeg><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, Ecur, c->d.row_ptr, c->d.eval_col,
+                                                c->d.eval_edge, c->m, F, ck.Fs, clip2);
         const dim3 bg((unsigned)c->n, (unsigned)ceil_div(F, kWFB));
         wbp_bit<<<bg, kWFB, 0, s>>>(ck.Rt, Ecur, d_w + (size_t)(t - 1) * c->nnz, Lcur, c->d.col_ptr,
-                                    c->d.col_edge, c->n, F, ck.Fs);
+                                    c->d.col_edge, c->d.col_pos, c->n, F, ck.Fs);
     }
     if (T == 0) {
         LDPC_TRY_CUDA(cudaMemcpyAsync(d_post, d_llr, sizeof(float) * (size_t)F * c->n,
@@ -433,7 +434,8 @@ int ldpc_decode_backward(const ldpc_code *c, int32_t F, int32_t T, const float *
         const float *Ecur = ck.E + (t - 1) * eF;
         const float *wcur = d_w + (size_t)(t - 1) * c->nnz;
         wbp_bit_back<<<bg, kWFB, 0, s>>>(wk.gOut, gX, Ecur, wcur, wk.gE, wk.gR, wk.gwpart, c->d.col_ptr,
-                                         c->d.col_edge, c->n, F, ck.Fs, t == T, t == T, (int32_t)c->nnz);
+                                         c->d.col_edge, c->d.col_pos, c->n, F, ck.Fs, t == T, t == T,
+                                         (int32_t)c->nnz);
         if (d_grad_w)
             wbp_reduce_w<<<(unsigned)ceil_div(c->nnz, 256), 256, 0, s>>>(
                 wk.gwpart, d_grad_w + (size_t)(t - 1) * c->nnz, wk.nfb, (int32_t)c->nnz);
@@ -441,9 +443,9 @@ int ldpc_decode_backward(const ldpc_code *c, int32_t F, int32_t T, const float *
         const float *Eprev = t == 1 ? nullptr : ck.E + (t - 2) * eF;
         const float *wprev = t == 1 ? nullptr : d_w + (size_t)(t - 2) * c->nnz;
         wbp_check_back<kWMaxDeg><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, wk.gE, gX, c->d.row_ptr,
-                                                     c->d.col_idx, c->m, F, ck.Fs, clip2);
+                                                     c->d.eval_col, c->d.eval_edge, c->m, F, ck.Fs, clip2);
     }
-    wbp_final_r<<<bg, kWFB, 0, s>>>(gX, wk.gR, c->d.col_ptr, c->d.col_edge, c->n, F, ck.Fs);
+    wbp_final_r<<<bg, kWFB, 0, s>>>(gX, wk.gR, c->d.col_ptr, c->d.col_pos, c->n, F, ck.Fs);
     if (d_grad_llr)
         from_interleaved<<<tgrid, dim3(32, 8), 0, s>>>(wk.gR, d_grad_llr, c->n, F, ck.Fs, kLog2e);
     LDPC_TRY_CUDA(cudaGetLastError());

@@ -107,3 +107,20 @@ def test_host_only_code_cannot_decode(L):
     assert st == -1
     assert b"host-only" in c._lib.ldpc_last_error()
     del torch
+
+
+@pytest.mark.parametrize("maker,conflict_free", [  # regular codes: nearly conflict-free
+    (lambda: S.random_regular(8064, 3, 6, seed=2), True),
+    (lambda: S.gallager_regular(504, 3, 6, seed=1), True),
+    (lambda: S.random_regular(2016, 3, 12, seed=47), True),
+    (lambda: S.dense_to_code(np.random.default_rng(5).integers(0, 2, (37, 70), dtype=np.uint8)), False),
+])
+def test_check_schedule_is_a_row_permutation(L, maker, conflict_free):
+    code = maker()
+    c = L.Code.from_csr_code(code, host_only=True)
+    order, unplaced = c.schedule()
+    for r in range(code.m):
+        lo, hi = code.row_ptr[r], code.row_ptr[r + 1]
+        assert sorted(order[lo:hi].tolist()) == list(range(lo, hi))
+    if conflict_free:   # at most 1 % of edges outside a conflict-free step
+        assert unplaced <= 0.01 * code.nnz, unplaced
