@@ -155,6 +155,22 @@ int ldpc_decode(const ldpc_code *code, const float *d_llr, int32_t F,
                 const ldpc_decode_opts *opts, float *d_post, uint32_t *d_hard, int32_t *d_iters,
                 uint8_t *d_ok, void *d_work, size_t work_bytes, ldpc_stream_t stream);
 
+/* ---- Decoding straight from host memory.  F frames of channel LLRs in host
+ * memory (h_llr, F x n; page-locked for the copies to overlap) are decoded
+ * in chunks of `chunk` frames: chunk i is copied to the device on a library
+ * upload stream while chunk i-1 is decoded on `stream`, and every chunk's
+ * outputs (each host pointer may be NULL) are copied back as soon as it is
+ * decoded.  When `stream` reaches the end of the queued work, every output is
+ * in host memory.  d_work holds ldpc_decode_host_workspace_size() bytes (two
+ * staging buffers and the decoder's own workspace).  The library's upload and
+ * download streams and their events are per device and shared: calls from several host threads at once
+ * on one device must be serialised by the caller. */
+int ldpc_decode_host_workspace_size(const ldpc_code *code, int32_t chunk, const ldpc_decode_opts *opts,
+                                    size_t *bytes);
+int ldpc_decode_host(const ldpc_code *code, const float *h_llr, int32_t F, const ldpc_decode_opts *opts,
+                     float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
+                     void *d_work, size_t work_bytes, ldpc_stream_t stream);
+
 /* ---- Mixed-code batches (serving): frames of several codes decoded in one
  * persistent launch.  A plan holds the codes (each regular with column weight
  * 3 and row weight 6, 9 or 12, at most 8192 bits, e.g. rates 1/2, 2/3, 3/4)

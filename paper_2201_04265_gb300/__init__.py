@@ -23,7 +23,7 @@ SCHED_AUTO, SCHED_PLAIN, SCHED_RESIDENT = 0, 1, 2
 _SCHED = {"auto": SCHED_AUTO, "plain": SCHED_PLAIN, "resident": SCHED_RESIDENT}
 
 __all__ = ["Code", "encode", "syndrome", "decode", "decode_noalloc", "decode_workspace_size", "DecodeResult",
-           "WeightedBP", "weighted_bp", "MixedPlan", "MixedBatch",
+           "WeightedBP", "weighted_bp", "MixedPlan", "MixedBatch", "HostDecoder",
            "LdpcError", "SCHED_AUTO", "SCHED_PLAIN", "SCHED_RESIDENT"]
 
 
@@ -393,3 +393,39 @@ class MixedPlan:
                                                  int(reps), _stream_handle(stream), ctypes.byref(cfg)),
                    "ldpc_mixed_autotune")
         return {"order": cfg.order, "groups_per_item": cfg.groups_per_item, "ctas_per_sm": cfg.ctas_per_sm}
+
+
+class HostDecoder:
+    """Decodes batches held in host memory, overlapping the copies with decoding
+    (ldpc_decode_host): chunk i is copied in while chunk i-1 is decoded and each
+    chunk's results are copied out as soon as they are ready."""
+
+    def __init__(self, code: Code, chunk: int = 8192, max_iters: int = 50, early_stop: bool = False,
+                 msg_fp16: bool = True, schedule="auto", clip: float = 20.0, device="cuda"):
+        self.code, self.chunk = code, int(chunk)
+        self.opts = _opts(max_iters, early_stop, msg_fp16, schedule, clip)
+        nb = ctypes.c_size_t()
+        _lib.check(code._lib.ldpc_decode_host_workspace_size(code.handle, self.chunk, ctypes.byref(self.opts),
+                                                             ctypes.byref(nb)), "ldpc_decode_host_workspace_size")
+        self.work = _workspace(nb.value, device, None)
+
+    def outputs(self, F: int, want_post: bool = False, want_hard: bool = True) -> DecodeResult:
+        """Page-locked host tensors for the results of F frames."""
+        return DecodeResult(
+            post=torch.empty((F, self.code.n), dtype=torch.float32, pin_memory=True) if want_post else None,
+            hard=torch.empty((F, self.code.NW), dtype=torch.int32, pin_memory=True) if want_hard else None,
+            iters=torch.empty((F,), dtype=torch.int32, pin_memory=True),
+            ok=torch.empty((F,), dtype=torch.uint8, pin_memory=True))
+
+    def decode(self, llr: torch.Tensor, out: DecodeResult | None = None, stream=None) -> DecodeResult:
+        """llr: float32 [F, n] on the host (page-locked for overlap).  The results
+        are in ``out`` once the stream has finished (synchronise it first)."""
+        if llr.is_cuda or llr.dtype != torch.float32 or not llr.is_contiguous() or llr.shape[1] != self.code.n:
+            raise ValueError("llr must be a contiguous float32 host tensor [F, n]")
+        F = llr.shape[0]
+        out = out if out is not None else self.outputs(F)
+        _lib.check(self.code._lib.ldpc_decode_host(self.code.handle, c_vp(llr.data_ptr()), F, ctypes.byref(self.opts),
+                                                   _ptr(out.post), _ptr(out.hard), _ptr(out.iters), _ptr(out.ok),
+                                                   self.chunk, _ptr(self.work), self.work.numel(),
+                                                   _stream_handle(stream)), "ldpc_decode_host")
+        return out

@@ -63,6 +63,9 @@ SIGNATURES = {
     "ldpc_decode_backward_workspace_size": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_size)]),
     "ldpc_decode_backward": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_f32, c_vp, c_size, c_vp, c_vp, c_vp, c_vp,
                                      c_size, c_vp]),
+    "ldpc_decode_host_workspace_size": (c_i32, [c_vp, c_i32, ctypes.POINTER(DecodeOpts), ctypes.POINTER(c_size)]),
+    "ldpc_decode_host": (c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(DecodeOpts), c_vp, c_vp, c_vp, c_vp, c_i32,
+                                 c_vp, c_size, c_vp]),
     "ldpc_mixed_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, c_i32, ctypes.POINTER(c_vp)]),
     "ldpc_mixed_destroy": (None, [c_vp]),
     "ldpc_mixed_workspace_size": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_size)]),

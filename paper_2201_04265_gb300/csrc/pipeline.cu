@@ -1,0 +1,156 @@
+// Decoding from host memory with copies overlapped with decoding.
+//
+// The batch is cut into chunks; chunk i's channel LLRs are copied to the
+// device on an upload stream while chunk i-1 is decoded on the caller's
+// stream, and each chunk's results are copied back on a download stream as
+// soon as it is decoded.  Two device staging buffers alternate, and events
+// order every reuse; uploads and downloads use separate streams so that an
+// upload never queues behind the previous chunk's download.  This is the host
+// side of the paper's batch processing (Sec. III-C) on one GPU: frames are
+// independent, so chunks are too.
+#include <map>
+#include <mutex>
+
+#include "ldpc_internal.h"
+
+namespace ldpc {
+namespace {
+
+struct CopyRes {
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t h2d[2] = {nullptr, nullptr}, dec[2] = {nullptr, nullptr}, d2h[2] = {nullptr, nullptr};
+};
+
+// Two copy streams and six events per device, created on first use.
+int copy_resources(CopyRes **out) {
+    static std::mutex mu;
+    static std::map<int, CopyRes> res;
+    int dev = -1;
+    LDPC_TRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = res.find(dev);
+    if (it == res.end()) {
+        CopyRes r;
+        LDPC_TRY_CUDA(cudaStreamCreateWithFlags(&r.up, cudaStreamNonBlocking));
+        LDPC_TRY_CUDA(cudaStreamCreateWithFlags(&r.down, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            LDPC_TRY_CUDA(cudaEventCreateWithFlags(&r.h2d[b], cudaEventDisableTiming));
+            LDPC_TRY_CUDA(cudaEventCreateWithFlags(&r.dec[b], cudaEventDisableTiming));
+            LDPC_TRY_CUDA(cudaEventCreateWithFlags(&r.d2h[b], cudaEventDisableTiming));
+        }
+        it = res.emplace(dev, r).first;
+    }
+    *out = &it->second;
+    return LDPC_OK;
+}
+
+struct PipeWs {
+    float *llr[2];
+    float *post[2];
+    uint32_t *hard[2];
+    int32_t *iters[2];
+    uint8_t *ok[2];
+    void *dec;
+    size_t dec_bytes;
+};
+
+size_t pipe_layout(const ldpc_code *c, int32_t chunk, const ldpc_decode_opts *o, PipeWs *w, void *base) {
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t at = off;
+        off += align256(b);
+        return at;
+    };
+    size_t oL[2], oP[2], oH[2], oI[2], oK[2];
+    for (int b = 0; b < 2; ++b) {
+        oL[b] = take(sizeof(float) * (size_t)chunk * c->n);
+        oP[b] = take(sizeof(float) * (size_t)chunk * c->n);
+        oH[b] = take(sizeof(uint32_t) * (size_t)chunk * c->NW);
+        oI[b] = take(sizeof(int32_t) * (size_t)chunk);
+        oK[b] = take((size_t)chunk);
+    }
+    size_t dec = 0;
+    ldpc_decode_workspace_size(c, chunk, o, &dec);
+    const size_t oD = take(dec);
+    if (w && base) {
+        char *p = static_cast<char *>(base);
+        for (int b = 0; b < 2; ++b) {
+            w->llr[b] = reinterpret_cast<float *>(p + oL[b]);
+            w->post[b] = reinterpret_cast<float *>(p + oP[b]);
+            w->hard[b] = reinterpret_cast<uint32_t *>(p + oH[b]);
+            w->iters[b] = reinterpret_cast<int32_t *>(p + oI[b]);
+            w->ok[b] = reinterpret_cast<uint8_t *>(p + oK[b]);
+        }
+        w->dec = p + oD;
+        w->dec_bytes = dec;
+    }
+    return off;
+}
+
+}  // namespace
+}  // namespace ldpc
+
+using namespace ldpc;
+
+extern "C" {
+
+int ldpc_decode_host_workspace_size(const ldpc_code *c, int32_t chunk, const ldpc_decode_opts *o,
+                                    size_t *bytes) {
+    if (!c || !o || !bytes || chunk < 1) return fail(LDPC_EINVAL, "bad arguments");
+    *bytes = pipe_layout(c, chunk, o, nullptr, nullptr);
+    return LDPC_OK;
+}
+
+int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ldpc_decode_opts *o,
+                     float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
+                     void *d_work, size_t work_bytes, ldpc_stream_t stream) {
+    if (!c || !o) return fail(LDPC_EINVAL, "code or opts is NULL");
+    if (F < 0 || chunk < 1) return fail(LDPC_EINVAL, "F < 0 or chunk < 1");
+    if (F == 0) return LDPC_OK;
+    if (!h_llr) return fail(LDPC_EINVAL, "h_llr is NULL");
+    PipeWs w{};
+    const size_t need = pipe_layout(c, chunk, o, &w, d_work);
+    if (!d_work || work_bytes < need) return fail(LDPC_EINVAL, "workspace too small (%zu < %zu)", work_bytes, need);
+    CopyRes *r = nullptr;
+    LDPC_TRY(copy_resources(&r));
+    cudaStream_t s = (cudaStream_t)stream;
+    // the copy streams start after everything already queued on the caller's stream
+    LDPC_TRY_CUDA(cudaEventRecord(r->dec[0], s));
+    LDPC_TRY_CUDA(cudaStreamWaitEvent(r->up, r->dec[0], 0));
+    LDPC_TRY_CUDA(cudaStreamWaitEvent(r->down, r->dec[0], 0));
+    const int64_t nchunks = ceil_div(F, chunk);
+    bool used[2] = {false, false};
+    for (int64_t ci = 0; ci < nchunks; ++ci) {
+        const int b = (int)(ci & 1);
+        const int64_t f0 = ci * chunk;
+        const int32_t fc = (int32_t)std::min<int64_t>(chunk, F - f0);
+        // staging buffer b is free once chunk ci-2's results are copied out
+        if (used[b]) LDPC_TRY_CUDA(cudaStreamWaitEvent(r->up, r->d2h[b], 0));
+        LDPC_TRY_CUDA(cudaMemcpyAsync(w.llr[b], h_llr + f0 * c->n, sizeof(float) * (size_t)fc * c->n,
+                                      cudaMemcpyHostToDevice, r->up));
+        LDPC_TRY_CUDA(cudaEventRecord(r->h2d[b], r->up));
+        LDPC_TRY_CUDA(cudaStreamWaitEvent(s, r->h2d[b], 0));
+        LDPC_TRY(ldpc_decode(c, w.llr[b], fc, o, h_post ? w.post[b] : nullptr, w.hard[b], w.iters[b], w.ok[b],
+                             w.dec, w.dec_bytes, stream));
+        LDPC_TRY_CUDA(cudaEventRecord(r->dec[b], s));
+        LDPC_TRY_CUDA(cudaStreamWaitEvent(r->down, r->dec[b], 0));
+        if (h_post)
+            LDPC_TRY_CUDA(cudaMemcpyAsync(h_post + f0 * c->n, w.post[b], sizeof(float) * (size_t)fc * c->n,
+                                          cudaMemcpyDeviceToHost, r->down));
+        if (h_hard)
+            LDPC_TRY_CUDA(cudaMemcpyAsync(h_hard + f0 * c->NW, w.hard[b], sizeof(uint32_t) * (size_t)fc * c->NW,
+                                          cudaMemcpyDeviceToHost, r->down));
+        if (h_iters)
+            LDPC_TRY_CUDA(cudaMemcpyAsync(h_iters + f0, w.iters[b], sizeof(int32_t) * (size_t)fc,
+                                          cudaMemcpyDeviceToHost, r->down));
+        if (h_ok)
+            LDPC_TRY_CUDA(cudaMemcpyAsync(h_ok + f0, w.ok[b], (size_t)fc, cudaMemcpyDeviceToHost, r->down));
+        LDPC_TRY_CUDA(cudaEventRecord(r->d2h[b], r->down));
+        used[b] = true;
+    }
+    // the caller's stream completes only after the last results reach the host
+    LDPC_TRY_CUDA(cudaStreamWaitEvent(s, r->d2h[(nchunks - 1) & 1], 0));
+    return LDPC_OK;
+}
+
+}  // extern "C"

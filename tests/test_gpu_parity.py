@@ -263,3 +263,27 @@ def test_resident_rejects_code_that_does_not_fit(L):
     with pytest.raises(L.LdpcError) as ei:
         L.decode(c, torch.zeros((2, c.n), device="cuda"), schedule="resident")
     assert ei.value.status == -5
+
+
+# ------------------------------------------------------ decode from host memory
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_decode_from_host_memory_equals_device_decode(L, pinned):
+    """ldpc_decode_host: chunked, copy-overlapped decoding from host memory gives
+    the same bits as ldpc_decode on the device (ragged last chunk included)."""
+    w = workload("reg36_1008", 1000, 2.0, seed=91)
+    c = dev_code(L, "reg36_1008")
+    host = torch.from_numpy(w.llr)
+    if pinned:
+        host = host.pin_memory()
+    dec = L.HostDecoder(c, chunk=384, max_iters=20, early_stop=True, msg_fp16=True)
+    out = dec.outputs(1000, want_post=True)
+    dec.decode(host, out=out)
+    torch.cuda.synchronize()
+    ref = L.decode(c, host.cuda(), max_iters=20, early_stop=True, msg_fp16=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.post.numpy(), ref.post.cpu().numpy())
+    np.testing.assert_array_equal(out.hard.numpy(), ref.hard.cpu().numpy())
+    np.testing.assert_array_equal(out.iters.numpy(), ref.iters.cpu().numpy())
+    np.testing.assert_array_equal(out.ok.numpy(), ref.ok.cpu().numpy())
