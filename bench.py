@@ -414,14 +414,17 @@ def run_profile_case(args):
     import ldpc_synth as S
     import paper_2201_04265_gb300 as L
     torch.cuda.set_device(0)
-    code = L.Code.from_csr_code(S.random_regular(N_BITS, DV, DC, seed=CODE_SEED))
+    if args.code == "qc":  # quasi-cyclic 46 x 68 base, 316 nonzeros, Z = 384 (n = 26112)
+        code = L.Code.from_qc(S.qc_base_matrix(46, 68, 316, 3, 19, 384, seed=3), 384)
+    else:
+        code = L.Code.from_csr_code(S.random_regular(N_BITS, DV, DC, seed=CODE_SEED))
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     llr = (torch.randn((args.frames, code.n), device="cuda", generator=g) * 3.0 + 2.5).contiguous()
     if args.profile_case == "resident":
         r = L.decode(code, llr, max_iters=ITERS, schedule="resident", msg_fp16=True, want_post=False)
     else:
-        r = L.decode(code, llr, max_iters=3, schedule="plain", msg_fp16=False, want_post=False)
+        r = L.decode(code, llr, max_iters=3, schedule="plain", msg_fp16=args.fp16, want_post=False)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile_case, "frames": args.frames, "ok_frames": int(r.ok.sum())}))
 
@@ -439,6 +442,8 @@ def main():
     ap.add_argument("--profile-case", choices=["resident", "plain"], default=None,
                     help="run one small decode (for ncu captures) instead of the benchmark")
     ap.add_argument("--frames", type=int, default=4096, help="frames of the --profile-case run")
+    ap.add_argument("--fp16", action="store_true", help="binary16 messages in the plain --profile-case run")
+    ap.add_argument("--code", choices=["c2", "qc"], default="c2", help="code of the --profile-case run")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

@@ -115,6 +115,42 @@ struct MsgVec<__half, 2> {
     }
 };
 
+// Raw (unconverted) message vectors, for loads issued well before use: the
+// widening to FP32 happens when the values are consumed.
+template <class T, int V>
+struct MsgRaw;
+template <>
+struct MsgRaw<float, 1> {
+    using R = float;
+    __device__ static R load(const float *p) { return *p; }
+    __device__ static void widen(R r, float *x) { x[0] = r; }
+};
+template <>
+struct MsgRaw<float, 2> {
+    using R = float2;
+    __device__ static R load(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ static void widen(R r, float *x) {
+        x[0] = r.x;
+        x[1] = r.y;
+    }
+};
+template <>
+struct MsgRaw<__half, 1> {
+    using R = __half;
+    __device__ static R load(const __half *p) { return *p; }
+    __device__ static void widen(R r, float *x) { x[0] = __half2float(r); }
+};
+template <>
+struct MsgRaw<__half, 2> {
+    using R = __half2;
+    __device__ static R load(const __half *p) { return *reinterpret_cast<const __half2 *>(p); }
+    __device__ static void widen(R r, float *x) {
+        const float2 v = __half22float2(r);
+        x[0] = v.x;
+        x[1] = v.y;
+    }
+};
+
 template <class T>
 __device__ __forceinline__ float msg_load(const T *p);
 template <>

@@ -107,19 +107,15 @@ template <class MsgT, int DMAX, int V>
 __device__ __forceinline__ void plain_check_load(const float *__restrict__ Lt,
                                                  const MsgT *__restrict__ Et,
                                                  const int32_t *__restrict__ col_idx, int e0, int d,
-                                                 int64_t Fs, int64_t f, int first, float (&L)[DMAX][V],
-                                                 float (&Eo)[DMAX][V]) {
+                                                 int64_t Fs, int64_t f, int first,
+                                                 typename MsgRaw<float, V>::R (&L)[DMAX],
+                                                 typename MsgRaw<MsgT, V>::R (&Eo)[DMAX]) {
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
         if (j < d) {
             const int v = __ldg(&col_idx[e0 + j]);
-            MsgVec<float, V>::load(Lt + (int64_t)v * Fs + f, L[j]);
-            if (first) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) Eo[j][i] = 0.f;
-            } else {
-                MsgVec<MsgT, V>::load(Et + (int64_t)(e0 + j) * Fs + f, Eo[j]);
-            }
+            L[j] = MsgRaw<float, V>::load(Lt + (int64_t)v * Fs + f);
+            if (!first) Eo[j] = MsgRaw<MsgT, V>::load(Et + (int64_t)(e0 + j) * Fs + f);
         }
     }
 }
@@ -141,7 +137,10 @@ plain_check(const float *__restrict__ Lt, MsgT *__restrict__ Et,
     for (int i = 0; i < V; ++i) bad[i] = 0;
     const int c0 = blockIdx.x * kCPB;
     const int ncheck = min(kCPB, m - c0);
-    float Ln[DMAX][V], En[DMAX][V];
+    // raw prefetch buffers: widened to FP32 only when the check is computed, so
+    // the next check's loads stay in flight during this check's arithmetic
+    typename MsgRaw<float, V>::R Ln[DMAX];
+    typename MsgRaw<MsgT, V>::R En[DMAX];
     int e0n = __ldg(&row_ptr[c0]);
     int dn = __ldg(&row_ptr[c0 + 1]) - e0n;
     plain_check_load<MsgT, DMAX, V>(Lt, Et, col_idx, e0n, dn, Fs, f, first, Ln, En);
@@ -149,12 +148,17 @@ plain_check(const float *__restrict__ Lt, MsgT *__restrict__ Et,
         const int e0 = e0n, d = dn;
         float L[DMAX][V], Eo[DMAX][V];
 #pragma unroll
-        for (int j = 0; j < DMAX; ++j)
+        for (int j = 0; j < DMAX; ++j) {
+            if (j < d) {
+                MsgRaw<float, V>::widen(Ln[j], L[j]);
+                if (first) {
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                L[j][i] = Ln[j][i];
-                Eo[j][i] = En[j][i];
+                    for (int i = 0; i < V; ++i) Eo[j][i] = 0.f;
+                } else {
+                    MsgRaw<MsgT, V>::widen(En[j], Eo[j]);
+                }
             }
+        }
         if (cc + 1 < ncheck) {
             e0n = __ldg(&row_ptr[c0 + cc + 1]);
             dn = __ldg(&row_ptr[c0 + cc + 2]) - e0n;
@@ -448,10 +452,12 @@ int run_plain(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_deco
         uint32_t *u_next = ws.unsat + ((t + 1) & 1) * ws.Fs;
         const int first = t == 1;
         const int check_syn = es && t >= 2;
-        if (c->dc_max <= 8) {
+        if (c->dc_max <= 6) {
+            launch_check<MsgT, 6, 2>(c, ws, F, clip2, first, check_syn, u_cur, s);
+        } else if (c->dc_max <= 8) {
             launch_check<MsgT, 8, 2>(c, ws, F, clip2, first, check_syn, u_cur, s);
         } else if (c->dc_max <= 16) {
-            launch_check<MsgT, 16, 2>(c, ws, F, clip2, first, check_syn, u_cur, s);
+            launch_check<MsgT, 16, 1>(c, ws, F, clip2, first, check_syn, u_cur, s);
         } else if (c->dc_max <= 32) {
             launch_check<MsgT, 32, 1>(c, ws, F, clip2, first, check_syn, u_cur, s);
         } else {
