@@ -1,0 +1,148 @@
+"""Parity at the benchmark sizes, on sampled frames the oracle recomputes one by one.
+
+n = 8064 random (3,6) code, 65536 frames, 50 fixed iterations (the benchmark
+batch): the GPU encodes every frame and decodes the whole batch in the
+benchmark's configuration (resident decoder, binary16 and FP32 messages).
+For a sample of frames the oracle regenerates the information bits and the
+noise from their per-frame seeds, encodes them itself (the GPU codeword must
+match bit for bit) and decodes them.  Quasi-cyclic n = 26112 code, 4096 frames,
+25 iterations: encoding is checked by properties that hold at any size, and
+decoding on the all-zero codeword (valid for every linear code), so no oracle
+input depends on the CUDA path.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import ldpc_synth as S
+import oracle
+from parity_util import fp32_conditioned_frames, hard_close, llr_close
+
+pytestmark = pytest.mark.gpu
+
+F2, T2, EBN0_2, SEED2 = 65536, 50, 2.0, 7100
+CH = 4096   # frames per host-side chunk, to bound host memory
+
+
+def _pack(bits):
+    return np.concatenate([S.pack_bits(bits[i:i + CH]) for i in range(0, bits.shape[0], CH)])
+
+
+def _unpack(words, n):
+    return np.concatenate([S.unpack_bits(words[i:i + CH], n) for i in range(0, words.shape[0], CH)])
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2201_04265_gb300 as L
+    torch.cuda.set_device(0)
+    return L
+
+
+@pytest.fixture(scope="module")
+def c2(L):
+    h = S.random_regular(8064, 3, 6, seed=2)
+    sysm = oracle.systematic(h)
+    code = L.Code.from_csr_code(h)
+    rate = sysm.k / h.n
+    # all frames: info bits and noise from per-frame seeds, GPU encoding
+    info = S.info_bits(F2, sysm.k, SEED2)
+    cw_words = L.encode(code, torch.from_numpy(_pack(info).view(np.int32)).cuda())
+    cw = _unpack(cw_words.cpu().numpy().view(np.uint32), h.n)
+    llr = np.empty((F2, h.n), dtype=np.float32)
+    for f0 in range(0, F2, 8192):
+        fr = np.arange(f0, f0 + 8192)
+        llr[f0:f0 + 8192] = S.bpsk_awgn_llr(cw[fr], EBN0_2, rate, S.frame_noise(F2, h.n, SEED2 + 1, frames=fr))
+    sample = np.random.default_rng(5).choice(F2, 12, replace=False)
+    return h, sysm, code, cw, torch.from_numpy(llr).cuda(), sample, rate
+
+
+def _oracle_frames(h, sysm, rate, frames):
+    msgs = S.info_bits(F2, sysm.k, SEED2, frames=frames)
+    cw = oracle.encode(sysm, msgs)
+    llr = S.bpsk_awgn_llr(cw, EBN0_2, rate, S.frame_noise(F2, h.n, SEED2 + 1, frames=frames))
+    return cw, llr
+
+
+def test_c2_encode_full_batch(L, c2):
+    h, sysm, code, cw, _, sample, rate = c2
+    want, _ = _oracle_frames(h, sysm, rate, sample)
+    np.testing.assert_array_equal(cw[sample], want)
+    # every codeword of the batch satisfies H c^T = 0 (Eq. 1)
+    _, ok = L.syndrome(code, torch.from_numpy(_pack(cw).view(np.int32)).cuda(), want_syn=False)
+    assert bool(ok.all())
+
+
+@pytest.mark.parametrize("fp16", [False, True])
+def test_c2_decode_full_batch_sampled_frames(L, c2, fp16):
+    h, sysm, code, cw, llr, sample, rate = c2
+    res = L.decode(code, llr, max_iters=T2, schedule="resident", msg_fp16=fp16)
+    torch.cuda.synchronize()
+    post = res.post.cpu().numpy()[sample]
+    hard = S.unpack_bits(res.hard.cpu().numpy()[sample].view(np.uint32), h.n)
+    ok = res.ok.cpu().numpy()[sample]
+    _, ollr = _oracle_frames(h, sysm, rate, sample)
+    np.testing.assert_array_equal(ollr, llr.cpu().numpy()[sample])   # identical inputs
+    ref = oracle.decode(h, ollr, iters=T2)
+    if not fp16:
+        stable, _ = fp32_conditioned_frames(h, ollr, T2)
+        assert stable.sum() >= 10
+        assert llr_close(post[stable], ref.post[stable]).all()
+        assert hard_close(hard[stable], ref.hard[stable], ref.post[stable]).all()
+        np.testing.assert_array_equal(ok[stable], ref.ok[stable])
+    else:
+        # binary16 storage: hard decisions of frames the oracle decodes agree
+        good = ref.ok.astype(bool)
+        np.testing.assert_array_equal(hard[good], ref.hard[good])
+    assert (res.iters.cpu().numpy() == T2).all()
+
+
+@pytest.fixture(scope="module")
+def qc(L):
+    base = S.qc_base_matrix(46, 68, 316, 3, 19, 384, seed=3)
+    return S.qc_expand(base, 384), L.Code.from_qc(base, 384)
+
+
+def test_qc_encode_full_batch_properties(L, qc):
+    h, code = qc
+    F = 4096
+    info = S.info_bits(F, code.k, 7300)
+    words = L.encode(code, torch.from_numpy(S.pack_bits(info).view(np.int32)).cuda())
+    _, ok = L.syndrome(code, words, want_syn=False)
+    assert bool(ok.all())                                   # H c^T = 0 for all 4096
+    bits = S.unpack_bits(words.cpu().numpy()[:64].view(np.uint32), code.n)
+    info_pos, _ = code.positions()
+    np.testing.assert_array_equal(bits[:, info_pos], info[:64])   # systematic
+    assert not oracle.syndrome(h, bits).any()               # checked by the oracle too
+
+
+def test_qc_decode_full_batch_sampled_frames(L, qc):
+    h, code = qc
+    F, T = 4096, 25
+    rate = code.k / code.n
+    zero = np.zeros((1, code.n), dtype=np.uint8)
+    llr = np.empty((F, code.n), dtype=np.float32)
+    for f0 in range(0, F, 1024):
+        fr = np.arange(f0, f0 + 1024)
+        llr[f0:f0 + 1024] = S.bpsk_awgn_llr(np.broadcast_to(zero, (1024, code.n)), 1.85, rate,
+                                            S.frame_noise(F, code.n, 7400, frames=fr))
+    d_llr = torch.from_numpy(llr).cuda()
+    r32 = L.decode(code, d_llr, max_iters=T, schedule="plain", msg_fp16=False)
+    r16 = L.decode(code, d_llr, max_iters=T, schedule="plain", msg_fp16=True)
+    torch.cuda.synchronize()
+    sample = np.random.default_rng(6).choice(F, 6, replace=False)
+    stable, ref = fp32_conditioned_frames(h, llr[sample], T)
+    assert stable.sum() >= 2
+    post = r32.post.cpu().numpy()[sample][stable]
+    hard32 = _unpack(r32.hard.cpu().numpy().view(np.uint32), code.n)
+    hard16 = _unpack(r16.hard.cpu().numpy().view(np.uint32), code.n)
+    assert llr_close(post, ref.post[stable]).all()
+    assert hard_close(hard32[sample][stable], ref.hard[stable], ref.post[stable]).all()
+    # frame errors against the all-zero codeword: binary16 storage may move
+    # only frames near the decoding threshold
+    fe32 = int(hard32.any(axis=1).sum())
+    fe16 = int(hard16.any(axis=1).sum())
+    assert abs(fe32 - fe16) <= 3 + 3 * np.sqrt(fe32), (fe32, fe16)
