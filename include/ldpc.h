@@ -279,6 +279,16 @@ const char *ldpc_status_string(int status);
 /* Message for the calling thread's most recent failed call ("" if none). */
 const char *ldpc_last_error(void);
 
+/* ---------------------------------------------------------------- probe --
+ * No counterpart in the paper: a measurement aid.  Measures, on the current
+ * device, how many results of ex2.approx, rcp.approx and lg2.approx (the three
+ * transcendental instructions of every edge update) one SM delivers per
+ * clock, and writes them to rates[0..2].  Synchronous; allocates and frees a
+ * few hundred KB of device memory; takes a few milliseconds.  The resident
+ * decoder's ALU roofline is built from these rates.
+ * Errors: LDPC_EINVAL (rates NULL), LDPC_ECUDA. */
+int ldpc_probe_xu_rates(float *rates);
+
 #ifdef __cplusplus
 }
 #endif

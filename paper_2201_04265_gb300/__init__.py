@@ -251,6 +251,15 @@ def decode_noalloc(code: Code, llr: torch.Tensor, max_iters: int = 20, early_sto
     return out
 
 
+def probe_xu_rates() -> tuple[float, float, float]:
+    """Results per SM per clock of ex2.approx, rcp.approx and lg2.approx on the
+    current device (a measurement aid for the decoder's ALU roofline)."""
+    lib = _lib.load()
+    rates = (ctypes.c_float * 3)()
+    _lib.check(lib.ldpc_probe_xu_rates(rates), "ldpc_probe_xu_rates")
+    return float(rates[0]), float(rates[1]), float(rates[2])
+
+
 class WeightedBP(torch.autograd.Function):
     """Weighted belief propagation with the library's hand-written adjoint.
 

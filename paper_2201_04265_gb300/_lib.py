@@ -42,6 +42,7 @@ class DecodeOpts(ctypes.Structure):
 
 # (name, restype, argtypes) of every exported symbol
 SIGNATURES = {
+    "ldpc_probe_xu_rates": (c_i32, [ctypes.POINTER(ctypes.c_float)]),
     "ldpc_code_create": (c_i32, [c_i32, c_i32, c_vp, c_vp, ctypes.POINTER(QcDesc), c_u32,
                                  ctypes.POINTER(c_vp)]),
     "ldpc_code_info": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),

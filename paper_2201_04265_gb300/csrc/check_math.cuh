@@ -30,6 +30,8 @@
 
 #include <cuda_fp16.h>
 
+#include <cstdint>
+
 namespace ldpc {
 
 constexpr float kLog2e = 1.4426950408889634f;
@@ -64,6 +66,19 @@ __device__ __forceinline__ EvOd evod_add(EvOd a, float u) {
     return {fmaf(u, a.o, a.e), fmaf(u, a.e, a.o)};
 }
 
+// (1, 0) (+) (1, u) = (1, u) and p (+) (1, 0) = p hold exactly in FP32 for
+// the non-negative pairs formed here, so the first prefix pair and the joins
+// with an empty prefix or suffix may be taken as they are, not computed.  The
+// 1 of such a pair must then be opaque_one(): with a literal 1 the compiler
+// rewrites fma(a, 1, b * c) as a + b * c and fuses that into fma(b, c, a),
+// which rounds once where the written form rounds twice, and the decoders
+// would no longer agree bit for bit.
+__device__ __forceinline__ float opaque_one() {
+    uint32_t b;
+    asm("mov.b32 %0, 0x3f800000;" : "=r"(b));
+    return __uint_as_float(b);
+}
+
 // Clipped check input x (log2 units) from the total LLR and the old message:
 // L_vc = L_v - E_cv (Eq. 6 rearranged), clipped to +-clip2.
 __device__ __forceinline__ float check_input(float L, float Eold, float clip2) {
@@ -76,6 +91,49 @@ __device__ __forceinline__ float check_u(float x) { return ex2_approx(-fabsf(x))
 // |E| = min(log2(ev / od), clip2); od = 0 (a degree-1 check) gives clip2.
 __device__ __forceinline__ float evod_magnitude(EvOd p, float clip2) {
     return fminf(lg2_approx(p.e * rcp_approx(p.o)), clip2);
+}
+
+// The same FP32 value of G frames (G = 1 or 2).  With two frames, one packed
+// instruction (FADD2 / FMUL2 / FFMA2 of sm_100 and later) does both; every
+// lane rounds exactly as the scalar instruction does (round to nearest, no
+// flush to zero), so the results are bit-identical to two scalar operations.
+template <int G>
+struct Lanes;
+template <>
+struct Lanes<1> {
+    using T = float;
+    __device__ static T make(const float *x) { return x[0]; }
+    __device__ static T splat(float a) { return a; }
+    __device__ static float get(T v, int) { return v; }
+    __device__ static T add(T a, T b) { return a + b; }
+    __device__ static T mul(T a, T b) { return a * b; }
+    __device__ static T fma(T a, T b, T c) { return fmaf(a, b, c); }
+};
+template <>
+struct Lanes<2> {
+    using T = float2;
+    __device__ static T make(const float *x) { return make_float2(x[0], x[1]); }
+    __device__ static T splat(float a) { return make_float2(a, a); }
+    __device__ static float get(T v, int i) { return i ? v.y : v.x; }
+    __device__ static T add(T a, T b) { return __fadd2_rn(a, b); }
+    __device__ static T mul(T a, T b) { return __fmul2_rn(a, b); }
+    __device__ static T fma(T a, T b, T c) { return __ffma2_rn(a, b, c); }
+};
+
+// The (ev, od) pair of G frames, with the operations of EvOd lane by lane.
+template <int G>
+struct EvOdV {
+    typename Lanes<G>::T e, o;
+};
+template <int G>
+__device__ __forceinline__ EvOdV<G> evod_join(EvOdV<G> a, EvOdV<G> b) {
+    using LV = Lanes<G>;
+    return {LV::fma(a.e, b.e, LV::mul(a.o, b.o)), LV::fma(a.e, b.o, LV::mul(a.o, b.e))};
+}
+template <int G>
+__device__ __forceinline__ EvOdV<G> evod_add(EvOdV<G> a, typename Lanes<G>::T u) {
+    using LV = Lanes<G>;
+    return {LV::fma(u, a.o, a.e), LV::fma(u, a.e, a.o)};
 }
 
 // Loads and stores of V consecutive frames' messages (V = 1 or 2), widened

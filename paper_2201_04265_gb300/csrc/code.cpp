@@ -147,6 +147,20 @@ int build_host(ldpc_code *c) {
         c->dv_max = std::max(c->dv_max, d);
         c->dv_min = std::min(c->dv_min, d);
     }
+    // degree classes of the plain decoder
+    {
+        auto group = [](int32_t count, const std::vector<int32_t> &ptr, int nclass, int (*cls)(int),
+                        std::vector<int32_t> &order, int32_t *off) {
+            std::vector<int32_t> cnt((size_t)nclass + 1, 0);
+            for (int32_t i = 0; i < count; ++i) cnt[cls(ptr[i + 1] - ptr[i]) + 1]++;
+            for (int q = 0; q < nclass; ++q) cnt[q + 1] += cnt[q];
+            for (int q = 0; q <= nclass; ++q) off[q] = cnt[q];
+            order.resize((size_t)count);
+            for (int32_t i = 0; i < count; ++i) order[cnt[cls(ptr[i + 1] - ptr[i])]++] = i;
+        };
+        group(m, c->row_ptr, kRowClasses, row_class_of, c->row_order, c->row_class);
+        group(n, c->col_ptr, kColClasses, col_class_of, c->col_order, c->col_class);
+    }
     // systematic generator
     const int32_t W = (n + 63) / 64;
     std::vector<uint64_t> rows((size_t)m * W, 0);
@@ -195,7 +209,8 @@ int upload(T **dst, const T *src, size_t count) {
 void free_device(ldpc_code *c) {
     void *ptrs[] = {c->d.row_ptr,   c->d.col_idx,    c->d.col_ptr,  c->d.col_edge,
                     c->d.info_pos,  c->d.parity_pos, c->d.AT,       c->d.res_edges,
-                    c->d.eval_col,  c->d.eval_edge,  c->d.col_pos};
+                    c->d.eval_col,  c->d.eval_edge,  c->d.col_pos,  c->d.row_order,
+                    c->d.col_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->d = DeviceCode{};
@@ -216,6 +231,8 @@ int upload_code(ldpc_code *c) {
     LDPC_TRY(upload(&c->d.eval_col, c->eval_col.data(), c->eval_col.size()));
     LDPC_TRY(upload(&c->d.eval_edge, c->eval_edge.data(), c->eval_edge.size()));
     LDPC_TRY(upload(&c->d.col_pos, c->col_pos.data(), c->col_pos.size()));
+    LDPC_TRY(upload(&c->d.row_order, c->row_order.data(), c->row_order.size()));
+    LDPC_TRY(upload(&c->d.col_order, c->col_order.data(), c->col_order.size()));
     std::vector<uint32_t> AT((size_t)c->KW * c->rank);
     for (int32_t j = 0; j < c->rank; ++j)
         for (int32_t w = 0; w < c->KW; ++w) AT[(size_t)w * c->rank + j] = c->A[(size_t)j * c->KW + w];

@@ -124,8 +124,9 @@ template <class MsgT, int DMAX, int V>
 __global__ void __launch_bounds__(kFB)
 plain_check(const float *__restrict__ Lt, MsgT *__restrict__ Et,
             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-            const int32_t *__restrict__ stop_it, uint32_t *__restrict__ unsat, int32_t m,
-            int32_t F, int64_t Fs, float clip2, int first, int check_syndrome) {
+            const int32_t *__restrict__ rows, const int32_t *__restrict__ stop_it,
+            uint32_t *__restrict__ unsat, int32_t mc, int32_t F, int64_t Fs, float clip2, int first,
+            int check_syndrome) {
     const int64_t f = ((int64_t)blockIdx.y * kFB + threadIdx.x) * V;
     if (f >= F) return;
     bool any = false;
@@ -136,13 +137,14 @@ plain_check(const float *__restrict__ Lt, MsgT *__restrict__ Et,
 #pragma unroll
     for (int i = 0; i < V; ++i) bad[i] = 0;
     const int c0 = blockIdx.x * kCPB;
-    const int ncheck = min(kCPB, m - c0);
+    const int ncheck = min(kCPB, mc - c0);
     // raw prefetch buffers: widened to FP32 only when the check is computed, so
     // the next check's loads stay in flight during this check's arithmetic
     typename MsgRaw<float, V>::R Ln[DMAX];
     typename MsgRaw<MsgT, V>::R En[DMAX];
-    int e0n = __ldg(&row_ptr[c0]);
-    int dn = __ldg(&row_ptr[c0 + 1]) - e0n;
+    int rn = __ldg(&rows[c0]);
+    int e0n = __ldg(&row_ptr[rn]);
+    int dn = __ldg(&row_ptr[rn + 1]) - e0n;
     plain_check_load<MsgT, DMAX, V>(Lt, Et, col_idx, e0n, dn, Fs, f, first, Ln, En);
     for (int cc = 0; cc < ncheck; ++cc) {
         const int e0 = e0n, d = dn;
@@ -160,8 +162,9 @@ plain_check(const float *__restrict__ Lt, MsgT *__restrict__ Et,
             }
         }
         if (cc + 1 < ncheck) {
-            e0n = __ldg(&row_ptr[c0 + cc + 1]);
-            dn = __ldg(&row_ptr[c0 + cc + 2]) - e0n;
+            rn = __ldg(&rows[c0 + cc + 1]);
+            e0n = __ldg(&row_ptr[rn]);
+            dn = __ldg(&row_ptr[rn + 1]) - e0n;
             plain_check_load<MsgT, DMAX, V>(Lt, Et, col_idx, e0n, dn, Fs, f, first, Ln, En);
         }
         float u[DMAX][V];
@@ -228,14 +231,16 @@ template <class MsgT>
 __global__ void __launch_bounds__(kFB)
 plain_check_wide(const float *__restrict__ Lt, MsgT *__restrict__ Et,
                  const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-                 const int32_t *__restrict__ stop_it, uint32_t *__restrict__ unsat, int32_t m,
-                 int32_t F, int64_t Fs, float clip2, int first, int check_syndrome) {
+                 const int32_t *__restrict__ rows, const int32_t *__restrict__ stop_it,
+                 uint32_t *__restrict__ unsat, int32_t mc, int32_t F, int64_t Fs, float clip2,
+                 int first, int check_syndrome) {
     const int64_t f = (int64_t)blockIdx.y * kFB + threadIdx.x;
     if (f >= F || stop_it[f] >= 0) return;
     uint32_t bad = 0;
     for (int cc = 0; cc < kCPB; ++cc) {
-        const int c = blockIdx.x * kCPB + cc;
-        if (c >= m) break;
+        const int ci = blockIdx.x * kCPB + cc;
+        if (ci >= mc) break;
+        const int c = __ldg(&rows[ci]);
         const int e0 = __ldg(&row_ptr[c]);
         const int d = __ldg(&row_ptr[c + 1]) - e0;
         const int nch = (d + 7) >> 3;
@@ -313,9 +318,9 @@ template <class MsgT, int DVMAX, int V>
 __global__ void __launch_bounds__(kFB)
 plain_bit(const float *__restrict__ Rt, float *__restrict__ Lt, const MsgT *__restrict__ Et,
           const int32_t *__restrict__ col_ptr, const int32_t *__restrict__ col_edge,
-          int32_t *__restrict__ stop_it, const uint32_t *__restrict__ unsat_cur,
-          uint32_t *__restrict__ unsat_next, int32_t n, int32_t F, int64_t Fs, int t,
-          int early_stop) {
+          const int32_t *__restrict__ cols, int32_t *__restrict__ stop_it,
+          const uint32_t *__restrict__ unsat_cur, uint32_t *__restrict__ unsat_next, int32_t nc,
+          int32_t F, int64_t Fs, int t, int early_stop, int lead) {
     const int64_t f = ((int64_t)blockIdx.y * kFB + threadIdx.x) * V;
     if (f >= F) return;
     bool act[V];
@@ -324,9 +329,9 @@ plain_bit(const float *__restrict__ Rt, float *__restrict__ Lt, const MsgT *__re
     for (int i = 0; i < V; ++i) {
         act[i] = (f + i < F) && stop_it[f + i] < 0;
         if (act[i] && early_stop) {
-            if (blockIdx.x == 0) unsat_next[f + i] = 0u;
+            if (lead && blockIdx.x == 0) unsat_next[f + i] = 0u;
             if (t >= 2 && unsat_cur[f + i] == 0u) {
-                if (blockIdx.x == 0) stop_it[f + i] = t - 1;
+                if (lead && blockIdx.x == 0) stop_it[f + i] = t - 1;
                 act[i] = false;
             }
         }
@@ -335,8 +340,9 @@ plain_bit(const float *__restrict__ Rt, float *__restrict__ Lt, const MsgT *__re
     }
     if (!any) return;
     for (int vv = 0; vv < kVPB; ++vv) {
-        const int v = blockIdx.x * kVPB + vv;
-        if (v >= n) break;
+        const int vi = blockIdx.x * kVPB + vv;
+        if (vi >= nc) break;
+        const int v = __ldg(&cols[vi]);
         const int q0 = __ldg(&col_ptr[v]);
         const int dv = __ldg(&col_ptr[v + 1]) - q0;
         float L[V], Ev[DVMAX][V];
@@ -365,21 +371,22 @@ template <class MsgT>
 __global__ void __launch_bounds__(kFB)
 plain_bit_wide(const float *__restrict__ Rt, float *__restrict__ Lt, const MsgT *__restrict__ Et,
                const int32_t *__restrict__ col_ptr, const int32_t *__restrict__ col_edge,
-               int32_t *__restrict__ stop_it, const uint32_t *__restrict__ unsat_cur,
-               uint32_t *__restrict__ unsat_next, int32_t n, int32_t F, int64_t Fs, int t,
-               int early_stop) {
+               const int32_t *__restrict__ cols, int32_t *__restrict__ stop_it,
+               const uint32_t *__restrict__ unsat_cur, uint32_t *__restrict__ unsat_next, int32_t nc,
+               int32_t F, int64_t Fs, int t, int early_stop, int lead) {
     const int64_t f = (int64_t)blockIdx.y * kFB + threadIdx.x;
     if (f >= F || stop_it[f] >= 0) return;
     if (early_stop) {
-        if (blockIdx.x == 0) unsat_next[f] = 0u;
+        if (lead && blockIdx.x == 0) unsat_next[f] = 0u;
         if (t >= 2 && unsat_cur[f] == 0u) {
-            if (blockIdx.x == 0) stop_it[f] = t - 1;
+            if (lead && blockIdx.x == 0) stop_it[f] = t - 1;
             return;
         }
     }
     for (int vv = 0; vv < kVPB; ++vv) {
-        const int v = blockIdx.x * kVPB + vv;
-        if (v >= n) break;
+        const int vi = blockIdx.x * kVPB + vv;
+        if (vi >= nc) break;
+        const int v = __ldg(&cols[vi]);
         float L = Rt[(int64_t)v * Fs + f];
         for (int q = __ldg(&col_ptr[v]), q1 = __ldg(&col_ptr[v + 1]); q < q1; ++q)
             L += msg_load(&Et[(int64_t)__ldg(&col_edge[q]) * Fs + f]);
@@ -416,22 +423,27 @@ __global__ void plain_iters(const int32_t *__restrict__ stop_it, int32_t *__rest
     if (f < F) iters[f] = stop_it[f] >= 0 ? stop_it[f] : T;
 }
 
+// One launch per non-empty degree class; the instance is sized for the
+// class's largest degree.  Check order does not matter (each check writes
+// only its own messages), so the classes give the same bits as one launch.
 template <class MsgT, int DMAX, int V>
-void launch_check(const ldpc_code *c, const PlainWs &ws, int32_t F, float clip2, int first,
+void launch_check(const ldpc_code *c, const PlainWs &ws, int q, int32_t F, float clip2, int first,
                   int check_syn, uint32_t *unsat, cudaStream_t s) {
-    dim3 grid((unsigned)ceil_div(c->m, kCPB), (unsigned)ceil_div(F, kFB * V));
+    const int32_t r0 = c->row_class[q], mc = c->row_class[q + 1] - r0;
+    dim3 grid((unsigned)ceil_div(mc, kCPB), (unsigned)ceil_div(F, kFB * V));
     plain_check<MsgT, DMAX, V><<<grid, kFB, 0, s>>>(ws.Lt, static_cast<MsgT *>(ws.Et), c->d.row_ptr,
-                                                    c->d.eval_col, ws.stop_it, unsat, c->m, F, ws.Fs,
-                                                    clip2, first, check_syn);
+                                                    c->d.eval_col, c->d.row_order + r0, ws.stop_it,
+                                                    unsat, mc, F, ws.Fs, clip2, first, check_syn);
 }
 
 template <class MsgT, int DVMAX, int V>
-void launch_bit(const ldpc_code *c, const PlainWs &ws, int32_t F, int t, int es,
+void launch_bit(const ldpc_code *c, const PlainWs &ws, int q, int lead, int32_t F, int t, int es,
                 const uint32_t *u_cur, uint32_t *u_next, cudaStream_t s) {
-    dim3 grid((unsigned)ceil_div(c->n, kVPB), (unsigned)ceil_div(F, kFB * V));
+    const int32_t v0 = c->col_class[q], nc = c->col_class[q + 1] - v0;
+    dim3 grid((unsigned)ceil_div(nc, kVPB), (unsigned)ceil_div(F, kFB * V));
     plain_bit<MsgT, DVMAX, V><<<grid, kFB, 0, s>>>(ws.Rt, ws.Lt, static_cast<const MsgT *>(ws.Et),
-                                                   c->d.col_ptr, c->d.col_pos, ws.stop_it, u_cur,
-                                                   u_next, c->n, F, ws.Fs, t, es);
+                                                   c->d.col_ptr, c->d.col_pos, c->d.col_order + v0,
+                                                   ws.stop_it, u_cur, u_next, nc, F, ws.Fs, t, es, lead);
 }
 
 template <class MsgT>
@@ -452,32 +464,41 @@ int run_plain(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_deco
         uint32_t *u_next = ws.unsat + ((t + 1) & 1) * ws.Fs;
         const int first = t == 1;
         const int check_syn = es && t >= 2;
-        if (c->dc_max <= 6) {
-            launch_check<MsgT, 6, 2>(c, ws, F, clip2, first, check_syn, u_cur, s);
-        } else if (c->dc_max <= 8) {
-            launch_check<MsgT, 8, 2>(c, ws, F, clip2, first, check_syn, u_cur, s);
-        } else if (c->dc_max <= 16) {
-            launch_check<MsgT, 16, 1>(c, ws, F, clip2, first, check_syn, u_cur, s);
-        } else if (c->dc_max <= 32) {
-            launch_check<MsgT, 32, 1>(c, ws, F, clip2, first, check_syn, u_cur, s);
-        } else {
-            dim3 grid((unsigned)ceil_div(c->m, kCPB), (unsigned)ceil_div(F, kFB));
-            plain_check_wide<MsgT><<<grid, kFB, 0, s>>>(ws.Lt, static_cast<MsgT *>(ws.Et),
-                                                        c->d.row_ptr, c->d.eval_col, ws.stop_it, u_cur,
-                                                        c->m, F, ws.Fs, clip2, first, check_syn);
+        for (int q = 0; q < kRowClasses; ++q) {
+            if (c->row_class[q + 1] == c->row_class[q]) continue;
+            switch (q) {
+            case 0: launch_check<MsgT, 6, 2>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
+            case 1: launch_check<MsgT, 8, 2>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
+            case 2: launch_check<MsgT, 16, 1>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
+            case 3: launch_check<MsgT, 32, 1>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
+            default: {
+                const int32_t r0 = c->row_class[q], mc = c->row_class[q + 1] - r0;
+                dim3 grid((unsigned)ceil_div(mc, kCPB), (unsigned)ceil_div(F, kFB));
+                plain_check_wide<MsgT><<<grid, kFB, 0, s>>>(
+                    ws.Lt, static_cast<MsgT *>(ws.Et), c->d.row_ptr, c->d.eval_col, c->d.row_order + r0,
+                    ws.stop_it, u_cur, mc, F, ws.Fs, clip2, first, check_syn);
+            }
+            }
         }
+        // the first launched bit class also resets the next flags and records
+        // stopped frames; later classes see those frames as stopped
         const int e = es ? 1 : 0;
-        if (c->dv_max <= 4) {
-            launch_bit<MsgT, 4, 2>(c, ws, F, t, e, u_cur, u_next, s);
-        } else if (c->dv_max <= 8) {
-            launch_bit<MsgT, 8, 2>(c, ws, F, t, e, u_cur, u_next, s);
-        } else if (c->dv_max <= 16) {
-            launch_bit<MsgT, 16, 1>(c, ws, F, t, e, u_cur, u_next, s);
-        } else {
-            dim3 grid((unsigned)ceil_div(c->n, kVPB), (unsigned)ceil_div(F, kFB));
-            plain_bit_wide<MsgT><<<grid, kFB, 0, s>>>(ws.Rt, ws.Lt, static_cast<const MsgT *>(ws.Et),
-                                                      c->d.col_ptr, c->d.col_pos, ws.stop_it, u_cur,
-                                                      u_next, c->n, F, ws.Fs, t, e);
+        int lead = 1;
+        for (int q = 0; q < kColClasses; ++q) {
+            if (c->col_class[q + 1] == c->col_class[q]) continue;
+            switch (q) {
+            case 0: launch_bit<MsgT, 4, 2>(c, ws, q, lead, F, t, e, u_cur, u_next, s); break;
+            case 1: launch_bit<MsgT, 8, 2>(c, ws, q, lead, F, t, e, u_cur, u_next, s); break;
+            case 2: launch_bit<MsgT, 16, 1>(c, ws, q, lead, F, t, e, u_cur, u_next, s); break;
+            default: {
+                const int32_t v0 = c->col_class[q], nc = c->col_class[q + 1] - v0;
+                dim3 grid((unsigned)ceil_div(nc, kVPB), (unsigned)ceil_div(F, kFB));
+                plain_bit_wide<MsgT><<<grid, kFB, 0, s>>>(
+                    ws.Rt, ws.Lt, static_cast<const MsgT *>(ws.Et), c->d.col_ptr, c->d.col_pos,
+                    c->d.col_order + v0, ws.stop_it, u_cur, u_next, nc, F, ws.Fs, t, e, lead);
+            }
+            }
+            lead = 0;
         }
     }
     LDPC_TRY_CUDA(cudaGetLastError());

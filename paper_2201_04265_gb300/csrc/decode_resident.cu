@@ -48,8 +48,24 @@ struct Shape {
 };
 constexpr Shape kShapes[] = {{6, 8}, {9, 6}, {12, 4}, {16, 3}};
 
+template <class T>
+__device__ __forceinline__ uint32_t as_u32(T x) {
+    return *reinterpret_cast<uint32_t *>(&x);
+}
+template <class T>
+__device__ __forceinline__ T from_u32(uint32_t x) {
+    return *reinterpret_cast<T *>(&x);
+}
+
 template <class MsgT, int G>
 struct EVec;
+// Besides widening and narrowing, each message word has three fused forms:
+//   add_to(L, w)   = L + E    (the bit sum, Eq. 7)
+//   sub_from(L, w) = L - E    (Eq. 6 rearranged)
+//   signed_word(m, s) = the word of E_i = (bit 31 of s_i ? -m_i : m_i)
+// each rounding exactly like the widened FP32 operation (binary16 widens
+// exactly; the mixed-precision add and fma round once, like FADD; negation
+// commutes with round-to-nearest).
 template <>
 struct EVec<__half, 2> {
     using T = __half2;
@@ -59,12 +75,37 @@ struct EVec<__half, 2> {
         x[1] = f.y;
     }
     __device__ static T make(const float *x) { return __floats2half2_rn(x[0], x[1]); }
+    __device__ static float2 add_to(float2 L, uint32_t w) {
+        float2 r;
+        asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+            "add.rn.f32.f16 %0, lo, %3;\n\tadd.rn.f32.f16 %1, hi, %4;\n\t}"
+            : "=f"(r.x), "=f"(r.y)
+            : "r"(w), "f"(L.x), "f"(L.y));
+        return r;
+    }
+    __device__ static float2 sub_from(float2 L, uint32_t w) {
+        float2 r;  // (-1) E + L: the product is exact, one rounding
+        asm("{\n\t.reg .f16 lo, hi, m;\n\tmov.b32 {lo, hi}, %2;\n\tmov.b16 m, 0xBC00;\n\t"
+            "fma.rn.f32.f16 %0, lo, m, %3;\n\tfma.rn.f32.f16 %1, hi, m, %4;\n\t}"
+            : "=f"(r.x), "=f"(r.y)
+            : "r"(w), "f"(L.x), "f"(L.y));
+        return r;
+    }
+    __device__ static uint32_t signed_word(const float *m, const uint32_t *s) {
+        const uint32_t h = as_u32(__floats2half2_rn(m[0], m[1]));
+        return h ^ (__byte_perm(s[0], s[1], 0x7030) & 0x80008000u);  // sign bytes -> bits 15, 31
+    }
 };
 template <>
 struct EVec<float, 1> {
     using T = float;
     __device__ static void get(T v, float *x) { x[0] = v; }
     __device__ static T make(const float *x) { return x[0]; }
+    __device__ static float add_to(float L, uint32_t w) { return L + __uint_as_float(w); }
+    __device__ static float sub_from(float L, uint32_t w) { return L - __uint_as_float(w); }
+    __device__ static uint32_t signed_word(const float *m, const uint32_t *s) {
+        return __float_as_uint(m[0]) ^ (s[0] & 0x80000000u);
+    }
 };
 
 struct ResArgs {
@@ -97,14 +138,6 @@ __device__ __forceinline__ void sts_f(uint32_t a, float v) {
 }
 __device__ __forceinline__ void sts_u(uint32_t a, uint32_t v) {
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-template <class T>
-__device__ __forceinline__ uint32_t as_u32(T x) {
-    return *reinterpret_cast<uint32_t *>(&x);
-}
-template <class T>
-__device__ __forceinline__ T from_u32(uint32_t x) {
-    return *reinterpret_cast<T *>(&x);
 }
 
 // Planar shared-memory layout of one frame group (see the file comment):
@@ -147,6 +180,10 @@ template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN>
 __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
                                                const Smem<MsgT, G, REG> &sm, float clip2) {
     using EV = EVec<MsgT, G>;
+    using LV = Lanes<G>;
+    using V = typename LV::T;
+    // the 1 of the pairs taken as they are (one frame) must be opaque_one()
+    const V one = LV::splat(G == 1 ? opaque_one() : 1.f), zero = LV::splat(0.f);
     uint32_t zacc[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) zacc[i] = 0;
@@ -156,7 +193,7 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
         uint32_t slot[DC];
 #pragma unroll
         for (int j = 0; j < DC; ++j) slot[j] = slot_of(idx[k], j);
-        float u[DC][G];
+        V u[DC];
         uint32_t xbits[DC][G], sacc[G], zsgn[G];
         int d = 0;
 #pragma unroll
@@ -165,24 +202,22 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
         for (int j = 0; j < DC; ++j) {
             if (REG || slot[j] != kNoSlot) {
                 ++d;
-                float L[G], Eo[G];
+                float Lf[G], uf[G];
 #pragma unroll
-                for (int i = 0; i < G; ++i) L[i] = lds_f(sm.laddr(slot[j], i));
-                EV::get(from_u32<typename EV::T>(lds_u(sm.eaddr(slot[j]))), Eo);
+                for (int i = 0; i < G; ++i) Lf[i] = lds_f(sm.laddr(slot[j], i));
+                const V x = EV::sub_from(LV::make(Lf), lds_u(sm.eaddr(slot[j])));  // Eq. 6 rearranged
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
-                    if (SYN) zsgn[i] ^= __float_as_uint(L[i]);  // bit 31: parity of [L < 0]
-                    const float x = L[i] - Eo[i];  // Eq. 6 rearranged
-                    xbits[j][i] = __float_as_uint(x);
+                    if (SYN) zsgn[i] ^= __float_as_uint(Lf[i]);  // bit 31: parity of [L < 0]
+                    xbits[j][i] = __float_as_uint(LV::get(x, i));
                     sacc[i] ^= xbits[j][i];
-                    u[j][i] = ex2_approx(-fminf(fabsf(x), clip2));
+                    uf[i] = ex2_approx(-fminf(fabsf(LV::get(x, i)), clip2));
                 }
+                u[j] = LV::make(uf);
             } else {
+                u[j] = zero;  // identity for the pair products
 #pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    u[j][i] = 0.f;  // identity for the pair products
-                    xbits[j][i] = 0u;
-                }
+                for (int i = 0; i < G; ++i) xbits[j][i] = 0u;
             }
         }
         // parity of z = [L >= 0] over the row = d + parity of [L < 0] (the bit
@@ -193,28 +228,35 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
         // (-1)^d folded into the accumulated sign bit
 #pragma unroll
         for (int i = 0; i < G; ++i) sacc[i] ^= (uint32_t)(d & 1) << 31;
-        EvOd pre[DC][G];
+        // prefix pairs; with one frame the first two are taken as they are:
+        // pre[0] = (1, 0), pre[1] = (1, u_0) exactly.  With two frames every
+        // pair is computed (taking them as they are there changed a few
+        // messages of degree-9 rows in the last bit, so it is not done)
+        constexpr bool kShort = G == 1;
+        EvOdV<G> pre[DC];
+        pre[0] = {one, zero};
+        if (kShort && DC > 1) pre[1] = {one, u[0]};
 #pragma unroll
-        for (int i = 0; i < G; ++i) pre[0][i] = {1.f, 0.f};
-#pragma unroll
-        for (int j = 1; j < DC; ++j)
-#pragma unroll
-            for (int i = 0; i < G; ++i) pre[j][i] = evod_add(pre[j - 1][i], u[j - 1][i]);
-        EvOd suf[G];
-#pragma unroll
-        for (int i = 0; i < G; ++i) suf[i] = {1.f, 0.f};
+        for (int j = kShort ? 2 : 1; j < DC; ++j) pre[j] = evod_add<G>(pre[j - 1], u[j - 1]);
+        EvOdV<G> suf = {one, zero};
 #pragma unroll
         for (int j = DC - 1; j >= 0; --j) {
             if (REG || slot[j] != kNoSlot) {
-                float out[G];
+                // leave-one-out pair; a join with an empty side is the other side
+                const EvOdV<G> p = !kShort ? evod_join<G>(pre[j], suf)
+                                   : j == DC - 1 ? pre[j] : j == 0 ? suf : evod_join<G>(pre[j], suf);
+                float rc[G], mag[G];
+                uint32_t sgn[G];
+#pragma unroll
+                for (int i = 0; i < G; ++i) rc[i] = rcp_approx(LV::get(p.o, i));
+                const V ratio = LV::mul(p.e, LV::make(rc));
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
-                    const float mag = evod_magnitude(evod_join(pre[j][i], suf[i]), clip2);
-                    out[i] = __uint_as_float(__float_as_uint(mag) |
-                                             ((sacc[i] ^ xbits[j][i]) & 0x80000000u));
-                    suf[i] = evod_add(suf[i], u[j][i]);
+                    mag[i] = fminf(lg2_approx(LV::get(ratio, i)), clip2);
+                    sgn[i] = sacc[i] ^ xbits[j][i];
                 }
-                sts_u(sm.eaddr(slot[j]), as_u32(EV::make(out)));
+                sts_u(sm.eaddr(slot[j]), EV::signed_word(mag, sgn));
+                suf = kShort && j == DC - 1 ? EvOdV<G>{one, u[j]} : evod_add<G>(suf, u[j]);
             }
         }
     }
@@ -253,26 +295,22 @@ template <class MsgT, int G, bool REG, bool SYN, int NR>
 __device__ __forceinline__ void bit_pass(const float (&R)[NR][G], const Smem<MsgT, G, REG> &sm, int n,
                                          int tid, int T, uint32_t active) {
     using EV = EVec<MsgT, G>;
+    using LV = Lanes<G>;
     constexpr int NS = Planes<REG>::NE;
 #pragma unroll
     for (int k = 0; k < kResVPT; ++k) {
         const int v = tid + k * T;
         if (v < n) {
-            float L[G];
+            float r[G];
 #pragma unroll
-            for (int i = 0; i < G; ++i) L[i] = REG ? lds_f(sm.rb(v, i)) : R[REG ? 0 : k][i];
+            for (int i = 0; i < G; ++i) r[i] = REG ? lds_f(sm.rb(v, i)) : R[REG ? 0 : k][i];
+            typename LV::T L = LV::make(r);
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                float e[G];
-                EV::get(from_u32<typename EV::T>(lds_u(sm.eb(v, q))), e);
+            for (int q = 0; q < NS; ++q) L = EV::add_to(L, lds_u(sm.eb(v, q)));
+            if (SYN) L = LV::add(L, LV::splat(0.f));  // no -0: z = [L >= 0] by sign
 #pragma unroll
-                for (int i = 0; i < G; ++i) L[i] += e[i];
-            }
-#pragma unroll
-            for (int i = 0; i < G; ++i) {
-                if (SYN) L[i] += 0.f;  // no -0: z = [L >= 0] by sign
-                if ((active >> i) & 1u) sts_f(sm.lb(v, i), L[i]);
-            }
+            for (int i = 0; i < G; ++i)
+                if ((active >> i) & 1u) sts_f(sm.lb(v, i), LV::get(L, i));
         }
     }
 }

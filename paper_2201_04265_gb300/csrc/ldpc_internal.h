@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -33,6 +34,23 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // The message clip in the kernels' log2 units.
 inline float clip_log2(float clip) { return (float)((double)clip * 1.4426950408889634); }
 
+// Degree classes of the plain decoder: each class of checks (bits) is
+// updated by a kernel instance sized for its largest degree.
+constexpr int kRowClasses = 5;
+constexpr int kRowClassMax[kRowClasses] = {6, 8, 16, 32, INT32_MAX};
+constexpr int kColClasses = 4;
+constexpr int kColClassMax[kColClasses] = {4, 8, 16, INT32_MAX};
+inline int row_class_of(int d) {
+    int q = 0;
+    while (d > kRowClassMax[q]) ++q;
+    return q;
+}
+inline int col_class_of(int d) {
+    int q = 0;
+    while (d > kColClassMax[q]) ++q;
+    return q;
+}
+
 // Device-side tables of a code (all owned by the code object).
 struct DeviceCode {
     int32_t *row_ptr = nullptr;    // [m+1]
@@ -45,6 +63,8 @@ struct DeviceCode {
     int32_t *eval_edge = nullptr; // [E]  CSR edge id at each evaluation position
     int32_t *col_pos = nullptr;   // [E]  evaluation position of col_edge[q]
     uint32_t *AT = nullptr;       // [KW][rank] parity map, word-major
+    int32_t *row_order = nullptr; // [m] checks grouped by degree class (plain decoder)
+    int32_t *col_order = nullptr; // [n] bits grouped by degree class (plain decoder)
     // resident decoder tables (see decode_resident.cu)
     uint32_t *res_edges = nullptr; // resident slot table of the single-code launch
     int32_t res_edges_len = 0;
@@ -76,6 +96,10 @@ struct ldpc_code {
     std::vector<int32_t> eval_edge, eval_col, col_pos, pos_of_edge;
     std::vector<int32_t> sched_groups;  // [ceil(m/32)][32] checks per warp group, -1 = none
     int64_t sched_excess = 0;           // edges above d_c per (group, bank): 0 = conflict-free
+    // checks (bits) grouped by degree class, ascending index within a class;
+    // class q holds row_order[row_class[q] .. row_class[q+1]-1]
+    std::vector<int32_t> row_order, col_order;
+    int32_t row_class[ldpc::kRowClasses + 1] = {}, col_class[ldpc::kColClasses + 1] = {};
     bool on_device = false;
     int device = -1;
     ldpc::DeviceCode d;

@@ -118,10 +118,14 @@ def test_mixed_autotune_graph_replay_and_bad_code(L, mixed):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         plan.decode(b, static_llr, out=out, workspace=ws)
+    # frame 7 (no valid code) leaves its output region unwritten: compare the rest
+    keep = np.ones(b.n_llr, dtype=bool)
+    o7 = int(b.llr_off[7])
+    keep[o7:o7 + codes[0].n] = False
     for scale in (1.0, 1.7):
         static_llr.copy_(llr * scale)
         g.replay()
         ref = plan.decode(b, llr * scale)
         torch.cuda.synchronize()
-        np.testing.assert_array_equal(out.post.cpu().numpy(), ref.post.cpu().numpy())
+        np.testing.assert_array_equal(out.post.cpu().numpy()[keep], ref.post.cpu().numpy()[keep])
         np.testing.assert_array_equal(out.iters.cpu().numpy(), ref.iters.cpu().numpy())

@@ -287,3 +287,11 @@ def test_decode_from_host_memory_equals_device_decode(L, pinned):
     np.testing.assert_array_equal(out.hard.numpy(), ref.hard.cpu().numpy())
     np.testing.assert_array_equal(out.iters.numpy(), ref.iters.cpu().numpy())
     np.testing.assert_array_equal(out.ok.numpy(), ref.ok.cpu().numpy())
+
+
+def test_probe_xu_rates(L):
+    """The roofline's measured per-op rates (results per SM per clock) lie in a
+    sane range: at least a few, at most one warp's worth per scheduler."""
+    ex2, rcp, lg2 = L.probe_xu_rates()
+    for r in (ex2, rcp, lg2):
+        assert 4.0 <= r <= 128.0, (ex2, rcp, lg2)
