@@ -292,6 +292,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(h, seconds=args.cpu_seconds)
+    table1 = paper_table1(L, torch, dev) if rank == 0 and not args.no_table1 else None
 
     if rank == 0:
         line = {
@@ -313,6 +314,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
             "cpu_baseline": cpu,
+            "paper_table1": table1,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -409,6 +411,62 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def paper_table1(L, torch, dev):
+    """The paper's own workload (Table I): n = 1032, 12 ones per row, 9/6/3 per
+    column (design rates 1/4, 1/2, 3/4), 10 decoding iterations, 1000 vectors.
+    Its metric is the per-vector time (total time / vectors), for batch
+    processing (all 1000 vectors in one call) and, as the GPU analogue of its
+    stream processing, one vector per call (latency).  Setup is untimed; each
+    figure is the median of 5 timed repetitions after a warm-up."""
+    import ldpc_synth as S
+    out = {"vectors": 1000, "iterations": 10, "ebn0_db": 2.0, "unit": "us per vector",
+           "decoder": "schedule auto (resident where the code fits, else plain), FP32 messages",
+           "single": "one vector per call: encode or decode latency in us"}
+    for rate in (0.25, 0.5, 0.75):
+        h = S.table1_code(rate, seed=6)
+        code = L.Code.from_csr_code(h)
+        F = 1000
+        g = torch.Generator(device=dev)
+        g.manual_seed(77)
+        info = torch.randint(0, 2 ** 32, (F, code.KW), dtype=torch.int64, device=dev, generator=g).to(torch.int32)
+        if code.k % 32:
+            info[:, -1] &= (1 << (code.k % 32)) - 1
+        cw = L.encode(code, info)
+        bits = ((cw.unsqueeze(-1) >> torch.arange(32, device=dev, dtype=torch.int32)) & 1)
+        bits = bits.reshape(F, -1)[:, :code.n].float()
+        s2 = 1.0 / (2 * (code.k / code.n) * 10 ** (2.0 / 10))
+        llr = (2 * ((2 * bits - 1) + s2 ** 0.5 * torch.randn((F, code.n), device=dev, generator=g)) / s2).contiguous()
+        kw = dict(max_iters=10, early_stop=False, want_post=False)
+
+        def timed(fn, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b) * 1e3)
+            return statistics.median(ts)
+
+        enc_b = timed(lambda: L.encode(code, info, out=cw)) / F
+        r = L.decode(code, llr, **kw)
+        dec_b = timed(lambda: L.decode(code, llr, out=r, **kw)) / F
+        info1, cw1, llr1 = info[:1].contiguous(), cw[:1].clone(), llr[:1].contiguous()
+        r1 = L.decode(code, llr1, **kw)
+        enc_1 = timed(lambda: L.encode(code, info1, out=cw1))
+        dec_1 = timed(lambda: L.decode(code, llr1, out=r1, **kw))
+        ok = float(r.ok.float().mean())
+        out[f"rate_{rate}"] = {"m": code.m, "k": code.k, "encode_batch": round(enc_b, 4),
+                               "decode_batch": round(dec_b, 4), "encode_single": round(enc_1, 2),
+                               "decode_single": round(dec_1, 2), "frames_ok": ok}
+        code.close()
+    return out
+
+
 def run_profile_case(args):
     """One decode of a small batch of the same code, for single-kernel ncu
     captures (inputs still larger than L2, a few hundred MB on the device)."""
@@ -442,6 +500,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-table1", action="store_true", help="skip the paper's Table I workload")
     ap.add_argument("--ref-frames-per-thread", type=int, default=4)
     ap.add_argument("--profile-case", choices=["resident", "plain"], default=None,
                     help="run one small decode (for ncu captures) instead of the benchmark")

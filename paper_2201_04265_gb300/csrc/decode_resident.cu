@@ -120,17 +120,22 @@ struct ResArgs {
     unsigned *counter;
 };
 
-// 32-bit shared-memory accesses (addresses in the shared window).
-// All shared accesses are volatile asm, so they keep their program order
-// relative to each other and to the barriers; stores also clobber memory.
+// 32-bit shared-memory accesses (addresses in the shared window).  Stores
+// are volatile and clobber memory, so they keep their order with each other
+// and with the barriers.  Loads are plain (not volatile) asm: the compiler may
+// schedule them early, which the passes allow because within a pass no
+// location is both written and read by different accesses (each message
+// belongs to one check, and L or R are only read).  A load may not move
+// across a barrier: its address is derived from the plane bases, which are
+// redefined after every barrier (Smem::fence).
 __device__ __forceinline__ float lds_f(uint32_t a) {
     float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
     return v;
 }
 __device__ __forceinline__ uint32_t lds_u(uint32_t a) {
     uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 __device__ __forceinline__ void sts_f(uint32_t a, float v) {
@@ -161,6 +166,9 @@ struct Smem {
     __device__ uint32_t eb(int v, int r) const { return e0 + r * plane + 4u * v; }
     __device__ uint32_t lb(int v, int i) const { return l0 + i * plane + 4u * v; }
     __device__ uint32_t rb(int v, int i) const { return l0 + (G + i) * plane + 4u * v; }
+    // after a barrier: the bases become new values to the compiler, so no
+    // shared load of the next pass can be placed before the barrier
+    __device__ void fence() { asm volatile("" : "+r"(e0), "+r"(l0)); }
 };
 
 template <class MsgT, int G, bool REG>
@@ -368,8 +376,9 @@ struct ResIO {
 // (check pass, bit pass), final syndrome, outputs.  Ends with a team barrier.
 template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, class Team, class IO>
 __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                             const Smem<MsgT, G, REG> &sm, int n, int npad,
+                                             const Smem<MsgT, G, REG> &sm_in, int n, int npad,
                                              const IO &io, int T_iters, float clip2) {
+    Smem<MsgT, G, REG> sm = sm_in;  // local copy: its bases are fenced at every barrier
     const int tid = tm.tid(), T = tm.size();
     const int lane = threadIdx.x & 31;
     uint32_t exists = 0;
@@ -394,7 +403,7 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
         }
     }
     for (int w = tid; w < Planes<REG>::NE * npad; w += T) sts_u(sm.e0 + 4u * w, 0u);
-    tm.sync();
+    { tm.sync(); sm.fence(); }
 
     uint32_t active = exists, okm = 0;
     int it_done[G];
@@ -412,13 +421,14 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
                     okm |= 1u << i;
                 }
             }
+            sm.fence();
             if (!active) break;
         } else {
             check_pass<MsgT, G, DC, CPT, REG, false>(idx, sm, clip2);
-            tm.sync();
+            { tm.sync(); sm.fence(); }
         }
         bit_pass<MsgT, G, REG, SYN>(R, sm, n, tid, T, active);
-        tm.sync();
+        { tm.sync(); sm.fence(); }
     }
     if (active) {  // frames that ran every iteration: syndrome of the final z
         const uint32_t bad = syndrome_pass<MsgT, G, DC, CPT, REG>(idx, sm);
@@ -430,6 +440,7 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
                 if (!any_bad) okm |= 1u << i;
             }
         }
+        sm.fence();
     }
     // outputs: total LLRs (natural units), packed hard decisions, counts
 #pragma unroll
@@ -455,7 +466,7 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
                 if (int32_t *it = io.iters(i)) *it = it_done[i];
                 if (uint8_t *okp = io.ok(i)) *okp = (uint8_t)((okm >> i) & 1u);
             }
-    tm.sync();
+    { tm.sync(); sm.fence(); }
 }
 
 template <class MsgT, int G, bool REG>
