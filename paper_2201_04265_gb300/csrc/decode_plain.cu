@@ -167,49 +167,47 @@ plain_check(const float *__restrict__ Lt, MsgT *__restrict__ Et,
             dn = __ldg(&row_ptr[rn + 1]) - e0n;
             plain_check_load<MsgT, DMAX, V>(Lt, Et, col_idx, e0n, dn, Fs, f, first, Ln, En);
         }
-        float u[DMAX][V];
+        using LV = Lanes<V>;
+        typename LV::T u[DMAX];  // positions beyond the degree: u = 0 (identity)
         uint32_t smask[V], zpar[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) smask[i] = zpar[i] = 0;
 #pragma unroll
         for (int j = 0; j < DMAX; ++j) {
+            float uj[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) uj[i] = 0.f;
             if (j < d) {
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     zpar[i] ^= (uint32_t)(L[j][i] >= 0.f);
                     const float x = check_input(L[j][i], Eo[j][i], clip2);
                     smask[i] |= (__float_as_uint(x) >> 31) << j;
-                    u[j][i] = check_u(x);
+                    uj[i] = check_u(x);
                 }
             }
+            u[j] = LV::make(uj);
         }
-        // prefix pairs pre[j] = (+) of inputs 0..j-1
-        EvOd pre[DMAX][V];
         uint32_t sall[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             bad[i] |= zpar[i];
-            pre[0][i] = {1.f, 0.f};
             sall[i] = (__popc(smask[i]) + d) & 1u;
         }
+        EvOdV<V> loo[DMAX];  // leave-one-out pairs
+        evod_leave_one_out<V, DMAX>(u, loo);
 #pragma unroll
-        for (int j = 1; j < DMAX; ++j)
-            if (j < d)
-#pragma unroll
-                for (int i = 0; i < V; ++i) pre[j][i] = evod_add(pre[j - 1][i], u[j - 1][i]);
-        EvOd suf[V];
-#pragma unroll
-        for (int i = 0; i < V; ++i) suf[i] = {1.f, 0.f};
-#pragma unroll
-        for (int j = DMAX - 1; j >= 0; --j) {
+        for (int j = 0; j < DMAX; ++j) {
             if (j < d) {
-                float out[V];
+                float out[V], rc[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) rc[i] = rcp_approx(LV::get(loo[j].o, i));
+                const typename LV::T ratio = LV::mul(loo[j].e, LV::make(rc));
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
-                    const float mag = evod_magnitude(evod_join(pre[j][i], suf[i]), clip2);
+                    const float mag = fminf(lg2_approx(LV::get(ratio, i)), clip2);
                     const uint32_t sgn = sall[i] ^ ((smask[i] >> j) & 1u);
                     out[i] = sgn ? -mag : mag;
-                    suf[i] = evod_add(suf[i], u[j][i]);
                 }
                 MsgVec<MsgT, V>::store(Et + (int64_t)(e0 + j) * Fs + f, out);
             }
@@ -469,8 +467,9 @@ int run_plain(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_deco
             switch (q) {
             case 0: launch_check<MsgT, 6, 2>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
             case 1: launch_check<MsgT, 8, 2>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
-            case 2: launch_check<MsgT, 16, 1>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
-            case 3: launch_check<MsgT, 32, 1>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
+            case 2: launch_check<MsgT, 12, 1>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
+            case 3: launch_check<MsgT, 16, 1>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
+            case 4: launch_check<MsgT, 32, 1>(c, ws, q, F, clip2, first, check_syn, u_cur, s); break;
             default: {
                 const int32_t r0 = c->row_class[q], mc = c->row_class[q + 1] - r0;
                 dim3 grid((unsigned)ceil_div(mc, kCPB), (unsigned)ceil_div(F, kFB));

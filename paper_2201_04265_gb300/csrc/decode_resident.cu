@@ -190,8 +190,7 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
     using EV = EVec<MsgT, G>;
     using LV = Lanes<G>;
     using V = typename LV::T;
-    // the 1 of the pairs taken as they are (one frame) must be opaque_one()
-    const V one = LV::splat(G == 1 ? opaque_one() : 1.f), zero = LV::splat(0.f);
+    const V zero = LV::splat(0.f);
     uint32_t zacc[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) zacc[i] = 0;
@@ -236,35 +235,22 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
         // (-1)^d folded into the accumulated sign bit
 #pragma unroll
         for (int i = 0; i < G; ++i) sacc[i] ^= (uint32_t)(d & 1) << 31;
-        // prefix pairs; with one frame the first two are taken as they are:
-        // pre[0] = (1, 0), pre[1] = (1, u_0) exactly.  With two frames every
-        // pair is computed (taking them as they are there changed a few
-        // messages of degree-9 rows in the last bit, so it is not done)
-        constexpr bool kShort = G == 1;
-        EvOdV<G> pre[DC];
-        pre[0] = {one, zero};
-        if (kShort && DC > 1) pre[1] = {one, u[0]};
+        EvOdV<G> loo[DC];  // leave-one-out pairs
+        evod_leave_one_out<G, DC>(u, loo);
 #pragma unroll
-        for (int j = kShort ? 2 : 1; j < DC; ++j) pre[j] = evod_add<G>(pre[j - 1], u[j - 1]);
-        EvOdV<G> suf = {one, zero};
-#pragma unroll
-        for (int j = DC - 1; j >= 0; --j) {
+        for (int j = 0; j < DC; ++j) {
             if (REG || slot[j] != kNoSlot) {
-                // leave-one-out pair; a join with an empty side is the other side
-                const EvOdV<G> p = !kShort ? evod_join<G>(pre[j], suf)
-                                   : j == DC - 1 ? pre[j] : j == 0 ? suf : evod_join<G>(pre[j], suf);
                 float rc[G], mag[G];
                 uint32_t sgn[G];
 #pragma unroll
-                for (int i = 0; i < G; ++i) rc[i] = rcp_approx(LV::get(p.o, i));
-                const V ratio = LV::mul(p.e, LV::make(rc));
+                for (int i = 0; i < G; ++i) rc[i] = rcp_approx(LV::get(loo[j].o, i));
+                const V ratio = LV::mul(loo[j].e, LV::make(rc));
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
                     mag[i] = fminf(lg2_approx(LV::get(ratio, i)), clip2);
                     sgn[i] = sacc[i] ^ xbits[j][i];
                 }
                 sts_u(sm.eaddr(slot[j]), EV::signed_word(mag, sgn));
-                suf = kShort && j == DC - 1 ? EvOdV<G>{one, u[j]} : evod_add<G>(suf, u[j]);
             }
         }
     }

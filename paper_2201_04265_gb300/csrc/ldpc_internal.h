@@ -36,8 +36,8 @@ inline float clip_log2(float clip) { return (float)((double)clip * 1.44269504088
 
 // Degree classes of the plain decoder: each class of checks (bits) is
 // updated by a kernel instance sized for its largest degree.
-constexpr int kRowClasses = 5;
-constexpr int kRowClassMax[kRowClasses] = {6, 8, 16, 32, INT32_MAX};
+constexpr int kRowClasses = 6;
+constexpr int kRowClassMax[kRowClasses] = {6, 8, 12, 16, 32, INT32_MAX};
 constexpr int kColClasses = 4;
 constexpr int kColClassMax[kColClasses] = {4, 8, 16, INT32_MAX};
 inline int row_class_of(int d) {

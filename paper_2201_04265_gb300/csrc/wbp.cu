@@ -145,10 +145,12 @@ wbp_check(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
     if (f >= F || c >= m) return;
     const int e0 = __ldg(&row_ptr[c]);
     const int d = __ldg(&row_ptr[c + 1]) - e0;
-    float u[DMAX];
+    float u[DMAX];  // positions beyond the degree: u = 0 (identity)
     uint32_t xb[DMAX], sacc = (uint32_t)(d & 1) << 31;
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
+        u[j] = 0.f;
+        xb[j] = 0u;
         if (j < d) {
             const int e = e0 + j;  // evaluation position
             const float L = Lprev[(int64_t)__ldg(&eval_col[e]) * Fs + f];
@@ -158,19 +160,14 @@ wbp_check(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
             u[j] = check_u(fminf(fmaxf(x, -clip2), clip2));
         }
     }
-    EvOd pre[DMAX];
-    pre[0] = {1.f, 0.f};
+    EvOdV<1> loo[DMAX];  // leave-one-out pairs
+    evod_leave_one_out<1, DMAX>(u, loo);
 #pragma unroll
-    for (int j = 1; j < DMAX; ++j)
-        if (j < d) pre[j] = evod_add(pre[j - 1], u[j - 1]);
-    EvOd suf = {1.f, 0.f};
-#pragma unroll
-    for (int j = DMAX - 1; j >= 0; --j) {
+    for (int j = 0; j < DMAX; ++j) {
         if (j < d) {
-            const float mag = evod_magnitude(evod_join(pre[j], suf), clip2);
-            Ecur[(int64_t)(e0 + j) * Fs + f] =
-                __uint_as_float(__float_as_uint(mag) | ((sacc ^ xb[j]) & 0x80000000u));
-            suf = evod_add(suf, u[j]);
+            const float mag = fminf(lg2_approx(__fmul_rn(loo[j].e, rcp_approx(loo[j].o))), clip2);
+            Ecur[(int64_t)(e0 + j) * Fs + f] =  // sign flip = negation, as in every decoder
+                __uint_as_float(__float_as_uint(mag) ^ ((sacc ^ xb[j]) & 0x80000000u));
         }
     }
 }
@@ -277,20 +274,15 @@ wbp_check_back(const float *__restrict__ Lprev, const float *__restrict__ Eprev,
         }
     }
     // leave-one-out pairs as in the forward, to get ev_j od_j and the output mask
-    EvOd pre[DMAX];
-    pre[0] = {1.f, 0.f};
+    EvOdV<1> loo[DMAX];
+    evod_leave_one_out<1, DMAX>(u, loo);
 #pragma unroll
-    for (int j = 1; j < DMAX; ++j)
-        if (j < d) pre[j] = evod_add(pre[j - 1], u[j - 1]);
-    EvOd suf = {1.f, 0.f};
-#pragma unroll
-    for (int j = DMAX - 1; j >= 0; --j) {
+    for (int j = 0; j < DMAX; ++j) {
         h[j] = 0.f;
         if (j < d) {
-            const EvOd p = evod_join(pre[j], suf);
-            const float raw = lg2_approx(p.e * rcp_approx(p.o));
+            const EvOdV<1> p = loo[j];
+            const float raw = lg2_approx(__fmul_rn(p.e, rcp_approx(p.o)));
             if (raw <= clip2 && p.o > 0.f) h[j] = gE[(int64_t)(e0 + j) * Fs + f] / (p.e * p.o);
-            suf = evod_add(suf, u[j]);
         }
     }
 #pragma unroll
