@@ -251,21 +251,30 @@ def run_ours(args):
         hdec.decode(host_llr[0], out=hout)  # warm-up
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for i in range(args.e2e_steps):
-            d_info.copy_(host_info, non_blocking=True)
-            L.encode(code, d_info, out=cw_out)
-            host_cw.copy_(cw_out, non_blocking=True)
-            hdec.decode(host_llr[i % len(EBN0)], out=hout)
-        b.record(stream)
-        barrier()
+        marks = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.e2e_steps)]
+        with ClockSampler(local) as e2e_clocks:
+            a.record(stream)
+            for i in range(args.e2e_steps):
+                marks[i][0].record(stream)
+                d_info.copy_(host_info, non_blocking=True)
+                L.encode(code, d_info, out=cw_out)
+                host_cw.copy_(cw_out, non_blocking=True)
+                marks[i][1].record(stream)
+                hdec.decode(host_llr[i % len(EBN0)], out=hout)
+                marks[i][2].record(stream)
+            b.record(stream)
+            barrier()
         e_ms = a.elapsed_time(b) / args.e2e_steps
+        enc_ms = [m[0].elapsed_time(m[1]) for m in marks]
+        hdec_ms = [m[1].elapsed_time(m[2]) for m in marks]
         h2d = host_llr[0].numel() * 4 + host_info.numel() * 4
         d2h = host_cw.numel() * 4 + hout.hard.numel() * 4 + hout.iters.numel() * 4 + hout.ok.numel()
         e2e = {"value": round(world * bits_per_step / (e_ms * 1e-3) / 1e9, 4), "unit": "Gbit/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(e_ms, 3), "steps": args.e2e_steps, "host_buffers_pinned": pinned,
-               "api": "encode + HostDecoder.decode (ldpc_decode_host, 8192-frame chunks)"}
+               "api": "encode + HostDecoder.decode (ldpc_decode_host, 8192-frame chunks)",
+               "encode_with_copies_ms": [round(x, 2) for x in enc_ms],
+               "host_decode_ms": [round(x, 2) for x in hdec_ms], "clocks": e2e_clocks.summary()}
 
     # --- roofline of the dominant kernel (the resident decoder): MUFU-bound
     dec_avg_s = statistics.mean(dec_ms) * 1e-3

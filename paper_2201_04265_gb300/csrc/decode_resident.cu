@@ -155,20 +155,36 @@ struct Planes {
     static constexpr bool RSM = REG;
 };
 
-template <class MsgT, int G, bool REG>
+// PL > 0: planes of 2^PL words known at compile time, so that every plane
+// offset is an immediate of the shared-memory instruction and one base
+// register serves all planes of a bit; PL = 0: the plane size is a run-time
+// value.
+template <class MsgT, int G, bool REG, int PL = 0>
 struct Smem {
-    uint32_t e0;     // shared address of message plane 0
-    uint32_t l0;     // shared address of the first total plane
-    uint32_t plane;  // bytes per plane, 4 P
-    uint32_t pmask;  // P - 1
+    uint32_t e0;      // shared address of message plane 0
+    uint32_t l0_;     // shared address of the first total plane (PL = 0)
+    uint32_t plane_;  // bytes per plane, 4 P (PL = 0)
+    uint32_t pmask_;  // P - 1 (PL = 0)
+    __device__ uint32_t plane() const {
+        if constexpr (PL > 0) return 4u << PL;
+        else return plane_;
+    }
+    __device__ uint32_t pmask() const {
+        if constexpr (PL > 0) return (1u << PL) - 1u;
+        else return pmask_;
+    }
+    __device__ uint32_t l0() const {
+        if constexpr (PL > 0) return e0 + Planes<REG>::NE * (4u << PL);
+        else return l0_;
+    }
     __device__ uint32_t eaddr(uint32_t s) const { return e0 + 4u * s; }
-    __device__ uint32_t laddr(uint32_t s, int i) const { return l0 + i * plane + 4u * (s & pmask); }
-    __device__ uint32_t eb(int v, int r) const { return e0 + r * plane + 4u * v; }
-    __device__ uint32_t lb(int v, int i) const { return l0 + i * plane + 4u * v; }
-    __device__ uint32_t rb(int v, int i) const { return l0 + (G + i) * plane + 4u * v; }
+    __device__ uint32_t laddr(uint32_t s, int i) const { return l0() + i * plane() + 4u * (s & pmask()); }
+    __device__ uint32_t eb(int v, int r) const { return e0 + r * plane() + 4u * v; }
+    __device__ uint32_t lb(int v, int i) const { return l0() + i * plane() + 4u * v; }
+    __device__ uint32_t rb(int v, int i) const { return l0() + (G + i) * plane() + 4u * v; }
     // after a barrier: the bases become new values to the compiler, so no
     // shared load of the next pass can be placed before the barrier
-    __device__ void fence() { asm volatile("" : "+r"(e0), "+r"(l0)); }
+    __device__ void fence() { asm volatile("" : "+r"(e0), "+r"(l0_)); }
 };
 
 template <class MsgT, int G, bool REG>
@@ -184,9 +200,9 @@ __device__ __forceinline__ uint32_t slot_of(const uint32_t *w, int j) {
 // at most DC edges with unused slots marked kNoSlot.  Updates the messages in
 // place.  With SYN, also returns bit i set when frame i has a check that the
 // hard decisions z = [L >= 0] (L as left by the last bit pass) do not satisfy.
-template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN>
+template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, class SM>
 __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                               const Smem<MsgT, G, REG> &sm, float clip2) {
+                                               const SM &sm, float clip2) {
     using EV = EVec<MsgT, G>;
     using LV = Lanes<G>;
     using V = typename LV::T;
@@ -262,9 +278,9 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
 }
 
 // Syndrome of z = [L >= 0] over the thread's checks (no message update).
-template <class MsgT, int G, int DC, int CPT, bool REG>
+template <class MsgT, int G, int DC, int CPT, bool REG, class SM>
 __device__ __forceinline__ uint32_t syndrome_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                                  const Smem<MsgT, G, REG> &sm) {
+                                                  const SM &sm) {
     uint32_t bad = 0;
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
@@ -285,8 +301,8 @@ __device__ __forceinline__ uint32_t syndrome_pass(const uint32_t (&idx)[CPT][(DC
 // frames not in `active` keep their L_v.  REG codes have exactly three edges
 // per bit and R on chip; otherwise all four planes are summed (unused slots
 // hold 0) and R comes from registers.
-template <class MsgT, int G, bool REG, bool SYN, int NR>
-__device__ __forceinline__ void bit_pass(const float (&R)[NR][G], const Smem<MsgT, G, REG> &sm, int n,
+template <class MsgT, int G, bool REG, bool SYN, int NR, class SM>
+__device__ __forceinline__ void bit_pass(const float (&R)[NR][G], const SM &sm, int n,
                                          int tid, int T, uint32_t active) {
     using EV = EVec<MsgT, G>;
     using LV = Lanes<G>;
@@ -360,11 +376,11 @@ struct ResIO {
 
 // Decodes one group of G frames with the team's threads: load R, iterate
 // (check pass, bit pass), final syndrome, outputs.  Ends with a team barrier.
-template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, class Team, class IO>
+template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, class Team, class IO, class SM>
 __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                             const Smem<MsgT, G, REG> &sm_in, int n, int npad,
+                                             const SM &sm_in, int n, int npad,
                                              const IO &io, int T_iters, float clip2) {
-    Smem<MsgT, G, REG> sm = sm_in;  // local copy: its bases are fenced at every barrier
+    SM sm = sm_in;  // local copy: its bases are fenced at every barrier
     const int tid = tm.tid(), T = tm.size();
     const int lane = threadIdx.x & 31;
     uint32_t exists = 0;
@@ -455,22 +471,22 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
     { tm.sync(); sm.fence(); }
 }
 
-template <class MsgT, int G, bool REG>
-__device__ __forceinline__ Smem<MsgT, G, REG> smem_at(unsigned char *base, int npad) {
-    Smem<MsgT, G, REG> sm;
+template <class MsgT, int G, bool REG, int PL = 0>
+__device__ __forceinline__ Smem<MsgT, G, REG, PL> smem_at(unsigned char *base, int npad) {
+    Smem<MsgT, G, REG, PL> sm;
     sm.e0 = (uint32_t)__cvta_generic_to_shared(base);
-    sm.plane = 4u * (uint32_t)npad;
-    sm.pmask = (uint32_t)npad - 1u;
-    sm.l0 = sm.e0 + Planes<REG>::NE * sm.plane;
+    sm.plane_ = 4u * (uint32_t)npad;
+    sm.pmask_ = (uint32_t)npad - 1u;
+    sm.l0_ = sm.e0 + Planes<REG>::NE * sm.plane_;
     return sm;
 }
 
-template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN>
+template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, int PL = 0>
 __global__ void __launch_bounds__(kResMaxThreads)
 resident_kernel(ResArgs a) {
     constexpr int DCW = (DC + 1) / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem<MsgT, G, REG> sm = smem_at<MsgT, G, REG>(smem_raw, a.npad);
+    const Smem<MsgT, G, REG, PL> sm = smem_at<MsgT, G, REG, PL>(smem_raw, a.npad);
     __shared__ int s_group;
     const int T = blockDim.x, tid = threadIdx.x;
     uint32_t idx[CPT][DCW];
@@ -506,6 +522,23 @@ template <class MsgT, int G, int DC, int CPT>
 KernelFn pick_flags(bool reg, bool syn) {
     if (reg) return syn ? resident_kernel<MsgT, G, DC, CPT, true, true> : resident_kernel<MsgT, G, DC, CPT, true, false>;
     return syn ? resident_kernel<MsgT, G, DC, CPT, false, true> : resident_kernel<MsgT, G, DC, CPT, false, false>;
+}
+
+// Regular (3,6) codes with binary16 messages -- the common long-code case --
+// also have instances with the plane size fixed at compile time (2^10 ..
+// 2^13 words); the results are the same bits.
+template <int PL>
+KernelFn pick_fixed_plane(bool syn) {
+    return syn ? resident_kernel<__half, 2, 6, 8, true, true, PL> : resident_kernel<__half, 2, 6, 8, true, false, PL>;
+}
+KernelFn pick_fixed(int npad, bool syn) {
+    switch (npad) {
+        case 1024: return pick_fixed_plane<10>(syn);
+        case 2048: return pick_fixed_plane<11>(syn);
+        case 4096: return pick_fixed_plane<12>(syn);
+        case 8192: return pick_fixed_plane<13>(syn);
+        default: return nullptr;
+    }
 }
 
 template <class MsgT, int G>
@@ -629,8 +662,11 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
     if (!d_work || work_bytes < 256) return fail(LDPC_EINVAL, "workspace too small (need 256 bytes)");
     const bool fp16 = o->msg_fp16 != 0;
     const bool syn = o->early_stop != 0 && o->max_iters >= 2;
-    KernelFn fn = fp16 ? pick_kernel<__half, 2>(c->res.dc_pad, c->res.regular, syn)
-                       : pick_kernel<float, 1>(c->res.dc_pad, c->res.regular, syn);
+    KernelFn fn = nullptr;
+    if (fp16 && c->res.regular && c->res.dc_pad == 6) fn = pick_fixed(pad_bits(c), syn);
+    if (!fn)
+        fn = fp16 ? pick_kernel<__half, 2>(c->res.dc_pad, c->res.regular, syn)
+                  : pick_kernel<float, 1>(c->res.dc_pad, c->res.regular, syn);
     if (!fn) return fail(LDPC_ENOTSUP, "no resident kernel for row degree %d", c->res.dc_pad);
     const int T = c->res.rows_pad;
     const size_t smem = res_smem(c, fp16, c->res.regular);

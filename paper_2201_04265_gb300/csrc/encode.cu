@@ -142,10 +142,21 @@ int launch_enc(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, int
 
 int launch_encode(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, int32_t F,
                   cudaStream_t s) {
+    // The widest frame tile that fits in shared memory and still gives every
+    // SM at least two blocks (fewer frames per block re-read A more often from
+    // L2, but a small batch of a long code would otherwise leave SMs idle);
+    // the result does not depend on the tile.
     constexpr size_t kMaxSmem = 200 * 1024;
-    if (enc_smem<32>(c) <= kMaxSmem) return launch_enc<32>(c, d_info, d_code, F, s);
-    if (enc_smem<16>(c) <= kMaxSmem) return launch_enc<16>(c, d_info, d_code, F, s);
-    if (enc_smem<8>(c) <= kMaxSmem) return launch_enc<8>(c, d_info, d_code, F, s);
+    int sms = 0;
+    LDPC_TRY(sm_count(&sms));
+    const int64_t want = 2 * (int64_t)sms;
+    const bool f32 = enc_smem<32>(c) <= kMaxSmem, f16 = enc_smem<16>(c) <= kMaxSmem,
+               f8 = enc_smem<8>(c) <= kMaxSmem;
+    if (f32 && ceil_div(F, 32) >= want) return launch_enc<32>(c, d_info, d_code, F, s);
+    if (f16 && ceil_div(F, 16) >= want) return launch_enc<16>(c, d_info, d_code, F, s);
+    if (f8) return launch_enc<8>(c, d_info, d_code, F, s);
+    if (f16) return launch_enc<16>(c, d_info, d_code, F, s);
+    if (f32) return launch_enc<32>(c, d_info, d_code, F, s);
     return fail(LDPC_ENOTSUP, "code too long for the encoder's shared-memory tile (n=%d)", c->n);
 }
 
