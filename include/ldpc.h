@@ -157,12 +157,13 @@ int ldpc_decode(const ldpc_code *code, const float *d_llr, int32_t F,
 
 /* ---- Decoding straight from host memory.  F frames of channel LLRs in host
  * memory (h_llr, F x n; page-locked for the copies to overlap) are decoded
- * in chunks of `chunk` frames: chunk i is copied to the device on a library
- * upload stream while chunk i-1 is decoded on `stream`, and every chunk's
- * outputs (each host pointer may be NULL) are copied back as soon as it is
- * decoded.  When `stream` reaches the end of the queued work, every output is
- * in host memory.  d_work holds ldpc_decode_host_workspace_size() bytes (two
- * staging buffers and the decoder's own workspace).  The library's upload and
+ * in chunks of `chunk` frames: chunks are copied to the device on a library
+ * upload stream up to two ahead of the chunk being decoded on `stream`, and
+ * every chunk's outputs (each host pointer may be NULL) are copied back as
+ * soon as it is decoded.  When `stream` reaches the end of the queued work,
+ * every output is in host memory.  d_work holds
+ * ldpc_decode_host_workspace_size() bytes (three staging buffers and the
+ * decoder's own workspace).  The library's upload and
  * download streams and their events are per device and shared: calls from several host threads at once
  * on one device must be serialised by the caller. */
 int ldpc_decode_host_workspace_size(const ldpc_code *code, int32_t chunk, const ldpc_decode_opts *opts,

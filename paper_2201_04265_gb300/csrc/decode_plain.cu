@@ -120,8 +120,14 @@ __device__ __forceinline__ void plain_check_load(const float *__restrict__ Lt,
     }
 }
 
+// Blocks per SM a check instance is compiled for (a register budget of
+// 65536 / (128 x blocks) per thread): the 16-wide one fits 4 blocks in 128
+// registers without spilling (3 blocks at its natural 133).
+template <int DMAX, int V>
+constexpr int check_min_blocks() { return DMAX == 16 && V == 1 ? 4 : 0; }  // 0: no minimum
+
 template <class MsgT, int DMAX, int V>
-__global__ void __launch_bounds__(kFB)
+__global__ void __launch_bounds__(kFB, check_min_blocks<DMAX, V>())
 plain_check(const float *__restrict__ Lt, MsgT *__restrict__ Et,
             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
             const int32_t *__restrict__ rows, const int32_t *__restrict__ stop_it,

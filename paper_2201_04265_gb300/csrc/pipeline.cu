@@ -3,9 +3,11 @@
 // The batch is cut into chunks; chunk i's channel LLRs are copied to the
 // device on an upload stream while chunk i-1 is decoded on the caller's
 // stream, and each chunk's results are copied back on a download stream as
-// soon as it is decoded.  Two device staging buffers alternate, and events
-// order every reuse; uploads and downloads use separate streams so that an
-// upload never queues behind the previous chunk's download.  This is the host
+// soon as it is decoded.  Three device staging buffers rotate, so an upload
+// may run up to two chunks ahead of the decoder and a copy slowed down by
+// other traffic on the host link is absorbed; events order every reuse, and
+// uploads and downloads use separate streams so that an upload never queues
+// behind the previous chunk's download.  This is the host
 // side of the paper's batch processing (Sec. III-C) on one GPU: frames are
 // independent, so chunks are too.
 #include <map>
@@ -16,12 +18,14 @@
 namespace ldpc {
 namespace {
 
+constexpr int kStage = 3;  // staging buffers
+
 struct CopyRes {
     cudaStream_t up = nullptr, down = nullptr;
-    cudaEvent_t h2d[2] = {nullptr, nullptr}, dec[2] = {nullptr, nullptr}, d2h[2] = {nullptr, nullptr};
+    cudaEvent_t h2d[kStage] = {}, dec[kStage] = {}, d2h[kStage] = {};
 };
 
-// Two copy streams and six events per device, created on first use.
+// Two copy streams and 3 kStage events per device, created on first use.
 int copy_resources(CopyRes **out) {
     static std::mutex mu;
     static std::map<int, CopyRes> res;
@@ -33,7 +37,7 @@ int copy_resources(CopyRes **out) {
         CopyRes r;
         LDPC_TRY_CUDA(cudaStreamCreateWithFlags(&r.up, cudaStreamNonBlocking));
         LDPC_TRY_CUDA(cudaStreamCreateWithFlags(&r.down, cudaStreamNonBlocking));
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kStage; ++b) {
             LDPC_TRY_CUDA(cudaEventCreateWithFlags(&r.h2d[b], cudaEventDisableTiming));
             LDPC_TRY_CUDA(cudaEventCreateWithFlags(&r.dec[b], cudaEventDisableTiming));
             LDPC_TRY_CUDA(cudaEventCreateWithFlags(&r.d2h[b], cudaEventDisableTiming));
@@ -45,11 +49,11 @@ int copy_resources(CopyRes **out) {
 }
 
 struct PipeWs {
-    float *llr[2];
-    float *post[2];
-    uint32_t *hard[2];
-    int32_t *iters[2];
-    uint8_t *ok[2];
+    float *llr[kStage];
+    float *post[kStage];
+    uint32_t *hard[kStage];
+    int32_t *iters[kStage];
+    uint8_t *ok[kStage];
     void *dec;
     size_t dec_bytes;
 };
@@ -61,8 +65,8 @@ size_t pipe_layout(const ldpc_code *c, int32_t chunk, const ldpc_decode_opts *o,
         off += align256(b);
         return at;
     };
-    size_t oL[2], oP[2], oH[2], oI[2], oK[2];
-    for (int b = 0; b < 2; ++b) {
+    size_t oL[kStage], oP[kStage], oH[kStage], oI[kStage], oK[kStage];
+    for (int b = 0; b < kStage; ++b) {
         oL[b] = take(sizeof(float) * (size_t)chunk * c->n);
         oP[b] = take(sizeof(float) * (size_t)chunk * c->n);
         oH[b] = take(sizeof(uint32_t) * (size_t)chunk * c->NW);
@@ -74,7 +78,7 @@ size_t pipe_layout(const ldpc_code *c, int32_t chunk, const ldpc_decode_opts *o,
     const size_t oD = take(dec);
     if (w && base) {
         char *p = static_cast<char *>(base);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kStage; ++b) {
             w->llr[b] = reinterpret_cast<float *>(p + oL[b]);
             w->post[b] = reinterpret_cast<float *>(p + oP[b]);
             w->hard[b] = reinterpret_cast<uint32_t *>(p + oH[b]);
@@ -119,12 +123,12 @@ int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ld
     LDPC_TRY_CUDA(cudaStreamWaitEvent(r->up, r->dec[0], 0));
     LDPC_TRY_CUDA(cudaStreamWaitEvent(r->down, r->dec[0], 0));
     const int64_t nchunks = ceil_div(F, chunk);
-    bool used[2] = {false, false};
+    bool used[kStage] = {};
     for (int64_t ci = 0; ci < nchunks; ++ci) {
-        const int b = (int)(ci & 1);
+        const int b = (int)(ci % kStage);
         const int64_t f0 = ci * chunk;
         const int32_t fc = (int32_t)std::min<int64_t>(chunk, F - f0);
-        // staging buffer b is free once chunk ci-2's results are copied out
+        // staging buffer b is free once chunk ci - kStage's results are copied out
         if (used[b]) LDPC_TRY_CUDA(cudaStreamWaitEvent(r->up, r->d2h[b], 0));
         LDPC_TRY_CUDA(cudaMemcpyAsync(w.llr[b], h_llr + f0 * c->n, sizeof(float) * (size_t)fc * c->n,
                                       cudaMemcpyHostToDevice, r->up));
@@ -149,7 +153,7 @@ int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ld
         used[b] = true;
     }
     // the caller's stream completes only after the last results reach the host
-    LDPC_TRY_CUDA(cudaStreamWaitEvent(s, r->d2h[(nchunks - 1) & 1], 0));
+    LDPC_TRY_CUDA(cudaStreamWaitEvent(s, r->d2h[(nchunks - 1) % kStage], 0));
     return LDPC_OK;
 }
 

@@ -34,7 +34,9 @@ CODES = {
     "reg39_1008": lambda: S.random_regular(1008, 3, 9, seed=41),
     "reg312_2016": lambda: S.random_regular(2016, 3, 12, seed=42),
     "reg36_1008": lambda: S.random_regular(1008, 3, 6, seed=5),
+    "table1_r025": lambda: S.table1_code(0.25, seed=6),
     "table1_r050": lambda: S.table1_code(0.5, seed=6),
+    "table1_r075": lambda: S.table1_code(0.75, seed=6),
     "irregular_37x70": lambda: S.dense_to_code(
         np.random.default_rng(5).integers(0, 2, (37, 70), dtype=np.uint8)),
     "qc_small": lambda: S.qc_expand(S.qc_base_matrix(8, 12, 40, 3, 8, 24, seed=3), 24),

@@ -120,6 +120,22 @@ def test_decode_fp32_few_iterations_all_frames(L, name, T):
         np.testing.assert_array_equal(post, w.llr)
 
 
+@pytest.mark.parametrize("name", ["table1_r025", "table1_r050", "table1_r075"])
+def test_decode_table1_paper_setting(L, name):
+    """The paper's Table I workload (n = 1032, 12 ones per row, 9/6/3 per
+    column, 10 fixed iterations) through the default schedule: the plain
+    decoder for column weights 9 and 6, the resident one for 3."""
+    w = workload(name, 200, 3.0, seed=31)
+    c = dev_code(L, name)
+    post, hard, iters, ok = _gpu_decode(L, c, w.llr, max_iters=10)
+    stable, ref = fp32_conditioned_frames(w.code, w.llr, 10)
+    assert stable.mean() > 0.8, stable.mean()
+    assert llr_close(post, ref.post)[stable].all()
+    assert hard_close(hard, ref.hard, ref.post)[stable].all()
+    np.testing.assert_array_equal(ok[stable], ref.ok[stable])
+    assert (iters == 10).all()
+
+
 @pytest.mark.parametrize("name,ebn0", [("c1_gallager_504", 2.0), ("reg312_2016", 3.5),
                                        ("table1_r050", 2.5)])
 def test_decode_fp32_fixed_20_iterations(L, name, ebn0):
