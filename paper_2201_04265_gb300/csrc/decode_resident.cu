@@ -40,6 +40,7 @@ constexpr int kResVPT = 16;       // bits per thread
 constexpr int kResMaxThreads = 512;
 constexpr size_t kSmemLimit = 226 * 1024;  // dynamic shared memory per CTA we allow ourselves
 constexpr int kResSlots = 4;      // message slots per bit (column degree <= 4)
+constexpr int kResSlotsWide = 9;  // ... for the wide-column instances (degree <= 9)
 constexpr uint32_t kNoSlot = 0xFFFFu;
 
 // Row shapes: padded row degree and checks per thread (about 48 edges/thread).
@@ -149,9 +150,9 @@ __device__ __forceinline__ void sts_u(uint32_t a, uint32_t v) {
 // NE message planes, then G planes of totals L, then (regular codes) G planes
 // of channel LLRs R.  Regular codes (three edges per bit) need three message
 // planes and keep R on chip, which frees the registers that would hold it.
-template <bool REG>
+template <bool REG, int NSL = kResSlots>
 struct Planes {
-    static constexpr int NE = REG ? 3 : kResSlots;
+    static constexpr int NE = REG ? 3 : NSL;
     static constexpr bool RSM = REG;
 };
 
@@ -159,8 +160,9 @@ struct Planes {
 // offset is an immediate of the shared-memory instruction and one base
 // register serves all planes of a bit; PL = 0: the plane size is a run-time
 // value.
-template <class MsgT, int G, bool REG, int PL = 0>
+template <class MsgT, int G, bool REG, int PL = 0, int NSL = kResSlots>
 struct Smem {
+    static constexpr int NE = Planes<REG, NSL>::NE;  // message planes
     uint32_t e0;      // shared address of message plane 0
     uint32_t l0_;     // shared address of the first total plane (PL = 0)
     uint32_t plane_;  // bytes per plane, 4 P (PL = 0)
@@ -174,7 +176,7 @@ struct Smem {
         else return pmask_;
     }
     __device__ uint32_t l0() const {
-        if constexpr (PL > 0) return e0 + Planes<REG>::NE * (4u << PL);
+        if constexpr (PL > 0) return e0 + NE * (4u << PL);
         else return l0_;
     }
     __device__ uint32_t eaddr(uint32_t s) const { return e0 + 4u * s; }
@@ -187,9 +189,9 @@ struct Smem {
     __device__ void fence() { asm volatile("" : "+r"(e0), "+r"(l0_)); }
 };
 
-template <class MsgT, int G, bool REG>
+template <class MsgT, int G, bool REG, int NSL = kResSlots>
 __host__ __device__ __forceinline__ size_t group_bytes(int npad) {
-    return (size_t)(Planes<REG>::NE + G + (Planes<REG>::RSM ? G : 0)) * 4u * npad;
+    return (size_t)(Planes<REG, NSL>::NE + G + (Planes<REG, NSL>::RSM ? G : 0)) * 4u * npad;
 }
 
 __device__ __forceinline__ uint32_t slot_of(const uint32_t *w, int j) {
@@ -306,7 +308,7 @@ __device__ __forceinline__ void bit_pass(const float (&R)[NR][G], const SM &sm, 
                                          int tid, int T, uint32_t active) {
     using EV = EVec<MsgT, G>;
     using LV = Lanes<G>;
-    constexpr int NS = Planes<REG>::NE;
+    constexpr int NS = SM::NE;
 #pragma unroll
     for (int k = 0; k < kResVPT; ++k) {
         const int v = tid + k * T;
@@ -404,7 +406,7 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
             }
         }
     }
-    for (int w = tid; w < Planes<REG>::NE * npad; w += T) sts_u(sm.e0 + 4u * w, 0u);
+    for (int w = tid; w < SM::NE * npad; w += T) sts_u(sm.e0 + 4u * w, 0u);
     { tm.sync(); sm.fence(); }
 
     uint32_t active = exists, okm = 0;
@@ -471,22 +473,22 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
     { tm.sync(); sm.fence(); }
 }
 
-template <class MsgT, int G, bool REG, int PL = 0>
-__device__ __forceinline__ Smem<MsgT, G, REG, PL> smem_at(unsigned char *base, int npad) {
-    Smem<MsgT, G, REG, PL> sm;
+template <class MsgT, int G, bool REG, int PL = 0, int NSL = kResSlots>
+__device__ __forceinline__ Smem<MsgT, G, REG, PL, NSL> smem_at(unsigned char *base, int npad) {
+    Smem<MsgT, G, REG, PL, NSL> sm;
     sm.e0 = (uint32_t)__cvta_generic_to_shared(base);
     sm.plane_ = 4u * (uint32_t)npad;
     sm.pmask_ = (uint32_t)npad - 1u;
-    sm.l0_ = sm.e0 + Planes<REG>::NE * sm.plane_;
+    sm.l0_ = sm.e0 + Planes<REG, NSL>::NE * sm.plane_;
     return sm;
 }
 
-template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, int PL = 0>
+template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, int PL = 0, int NSL = kResSlots>
 __global__ void __launch_bounds__(kResMaxThreads)
 resident_kernel(ResArgs a) {
     constexpr int DCW = (DC + 1) / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem<MsgT, G, REG, PL> sm = smem_at<MsgT, G, REG, PL>(smem_raw, a.npad);
+    const Smem<MsgT, G, REG, PL, NSL> sm = smem_at<MsgT, G, REG, PL, NSL>(smem_raw, a.npad);
     __shared__ int s_group;
     const int T = blockDim.x, tid = threadIdx.x;
     uint32_t idx[CPT][DCW];
@@ -558,10 +560,21 @@ int pad_bits(const ldpc_code *c) {
     return p;
 }
 
-size_t res_smem(const ldpc_code *c, bool fp16, bool reg) {
+size_t res_smem(const ldpc_code *c, bool fp16, bool reg, int slots = kResSlots) {
     const int P = pad_bits(c);
     if (reg) return fp16 ? group_bytes<__half, 2, true>(P) : group_bytes<float, 1, true>(P);
+    if (slots == kResSlotsWide)
+        return fp16 ? group_bytes<__half, 2, false, kResSlotsWide>(P) : group_bytes<float, 1, false, kResSlotsWide>(P);
     return fp16 ? group_bytes<__half, 2, false>(P) : group_bytes<float, 1, false>(P);
+}
+
+// Message slots per bit of a code's resident layout: 4, or 9 for the
+// wide-column instances (instantiated for rows of up to 12 edges, the paper's
+// Table I codes with 6 or 9 ones per column); 0 if neither fits.
+int res_slots(const ldpc_code *c) {
+    if (c->dv_max <= kResSlots) return kResSlots;
+    if (c->dv_max <= kResSlotsWide && c->dc_max > 9 && c->dc_max <= 12) return kResSlotsWide;
+    return 0;
 }
 
 // Edge-slot table for a team of T threads: [CPT * DCW][T] 32-bit words, two
@@ -602,7 +615,8 @@ std::vector<uint32_t> build_slot_table(const ldpc_code *c, int dc, int cpt, int 
 
 const Shape *pick_shape(const ldpc_code *c) {
     // slots up to (slots - 1) P + n - 1 must stay below the 16-bit empty mark
-    if (c->dv_max > kResSlots || (int64_t)(kResSlots - 1) * pad_bits(c) + c->n > 0xFFFE) return nullptr;
+    const int slots = res_slots(c);
+    if (!slots || (int64_t)(slots - 1) * pad_bits(c) + c->n > 0xFFFE) return nullptr;
     for (const Shape &s : kShapes)
         if (s.dc >= c->dc_max) return &s;
     return nullptr;
@@ -641,7 +655,7 @@ int build_resident_plan(ldpc_code *c) {
     p.edges = build_slot_table(c, shape->dc, shape->cpt, T);
     if (p.edges.empty()) return LDPC_OK;
     p.dc_pad = shape->dc;
-    p.dv_pad = kResSlots;
+    p.dv_pad = res_slots(c);
     p.rows_pad = T;  // thread count of the launch
     // exactly dc edges per check and three per bit: the specialised kernels
     p.regular = c->dc_min == shape->dc && c->dc_max == shape->dc && c->dv_min == 3 && c->dv_max == 3;
@@ -651,7 +665,7 @@ int build_resident_plan(ldpc_code *c) {
 
 bool resident_fits(const ldpc_code *c, const ldpc_decode_opts *o) {
     if (!c->res.ok) return false;
-    return res_smem(c, o->msg_fp16 != 0, c->res.regular) <= kSmemLimit;
+    return res_smem(c, o->msg_fp16 != 0, c->res.regular, c->res.dv_pad) <= kSmemLimit;
 }
 
 size_t resident_workspace(const ldpc_code *, int32_t, const ldpc_decode_opts *) { return 256; }
@@ -664,12 +678,19 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
     const bool syn = o->early_stop != 0 && o->max_iters >= 2;
     KernelFn fn = nullptr;
     if (fp16 && c->res.regular && c->res.dc_pad == 6) fn = pick_fixed(pad_bits(c), syn);
+    if (c->res.dv_pad == kResSlotsWide) {
+        if (c->res.dc_pad != 12) return fail(LDPC_ENOTSUP, "no wide-column resident kernel for rows of %d", c->res.dc_pad);
+        fn = fp16 ? (syn ? resident_kernel<__half, 2, 12, 4, false, true, 0, kResSlotsWide>
+                         : resident_kernel<__half, 2, 12, 4, false, false, 0, kResSlotsWide>)
+                  : (syn ? resident_kernel<float, 1, 12, 4, false, true, 0, kResSlotsWide>
+                         : resident_kernel<float, 1, 12, 4, false, false, 0, kResSlotsWide>);
+    }
     if (!fn)
         fn = fp16 ? pick_kernel<__half, 2>(c->res.dc_pad, c->res.regular, syn)
                   : pick_kernel<float, 1>(c->res.dc_pad, c->res.regular, syn);
     if (!fn) return fail(LDPC_ENOTSUP, "no resident kernel for row degree %d", c->res.dc_pad);
     const int T = c->res.rows_pad;
-    const size_t smem = res_smem(c, fp16, c->res.regular);
+    const size_t smem = res_smem(c, fp16, c->res.regular, c->res.dv_pad);
     int sms = 0, per_sm = 0;
     LDPC_TRY(sm_count(&sms));
     LDPC_TRY(kernel_setup((const void *)fn, T, smem, &per_sm));
