@@ -280,6 +280,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(e_ms, 3), "steps": args.e2e_steps, "host_buffers_pinned": pinned,
                "api": "encode + HostDecoder.decode (ldpc_decode_host, 8192-frame chunks)",
+               "median_ms_per_step": round(statistics.median([x + y for x, y in zip(enc_ms, hdec_ms)]), 3),
                "encode_with_copies_ms": [round(x, 2) for x in enc_ms],
                "host_decode_ms": [round(x, 2) for x in hdec_ms], "clocks": e2e_clocks.summary()}
 
