@@ -236,7 +236,8 @@ int ldpc_wbp_checkpoint_size(const ldpc_code *code, int32_t F, int32_t T, size_t
 
 /* Forward pass: d_llr F x n, d_w T x nnz, d_post F x n receives L^T (natural
  * units).  d_ckpt (>= ldpc_wbp_checkpoint_size bytes, 256-byte aligned) keeps
- * the per-iteration state for the backward pass.  Row degree <= 8. */
+ * the per-iteration state for the backward pass.  Row degree <= 8, column
+ * degree <= 32 (LDPC_ENOTSUP otherwise). */
 int ldpc_wbp_forward(const ldpc_code *code, const float *d_llr, int32_t F, int32_t T,
                      const float *d_w, float clip, float *d_post, void *d_ckpt, size_t ckpt_bytes,
                      ldpc_stream_t stream);

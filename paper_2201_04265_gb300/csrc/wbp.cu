@@ -37,6 +37,7 @@ namespace {
 
 constexpr int kWFB = 128;  // frames (threads) per block
 constexpr int kWMaxDeg = 8;
+constexpr int kWMaxCol = 32;  // column weight bound of the backward bit kernel
 
 struct WbpCkpt {
     float *Rt;  // [n][Fs]
@@ -203,7 +204,7 @@ wbp_bit_back(const float *__restrict__ gout2, const float *__restrict__ gX,
              float *__restrict__ gR, float *__restrict__ gwpart, const int32_t *__restrict__ col_ptr,
              const int32_t *__restrict__ col_edge, const int32_t *__restrict__ col_pos, int32_t n,
              int32_t F, int64_t Fs, int last, int first_acc, int32_t nnz) {
-    __shared__ float red[kWFB / 32];
+    __shared__ float red[kWMaxCol * (kWFB / 32)];
     const int64_t f = (int64_t)blockIdx.y * kWFB + threadIdx.x;
     const int v = blockIdx.x;
     const bool live = f < F;
@@ -218,26 +219,28 @@ wbp_bit_back(const float *__restrict__ gout2, const float *__restrict__ gX,
         const int64_t iv = (int64_t)v * Fs + f;
         gR[iv] = first_acc ? gL : gR[iv] + gL;
     }
+    // weight-gradient partials: each warp reduces every edge of the bit by
+    // shuffles, then one barrier, then thread q sums edge q over the warps in
+    // order (the same order of additions as one reduction per edge)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = q0; q < q1; ++q) {
-        const int e = __ldg(&col_edge[q]);  // CSR edge: weight and gradient index
         float contrib = 0.f;
         if (live) {
             const int64_t ie = (int64_t)__ldg(&col_pos[q]) * Fs + f;
             const float g = last ? gL : gL - gX[ie];
-            gE[ie] = __ldg(&wcur[e]) * g;
+            gE[ie] = __ldg(&wcur[__ldg(&col_edge[q])]) * g;
             contrib = Ecur[ie] * g;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, off);
-        if (lane == 0) red[warp] = contrib;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float s = 0.f;
-            for (int w = 0; w < kWFB / 32; ++w) s += red[w];
-            gwpart[(int64_t)blockIdx.y * nnz + e] = s;
-        }
-        __syncthreads();
+        if (lane == 0) red[(q - q0) * (kWFB / 32) + warp] = contrib;
+    }
+    __syncthreads();
+    const int q = q0 + (int)threadIdx.x;
+    if (q < q1) {
+        float sum = 0.f;
+        for (int w = 0; w < kWFB / 32; ++w) sum += red[(q - q0) * (kWFB / 32) + w];
+        gwpart[(int64_t)blockIdx.y * nnz + __ldg(&col_edge[q])] = sum;
     }
 }
 
@@ -332,6 +335,7 @@ int check_wbp_args(const ldpc_code *c, int32_t F, int32_t T, float clip) {
     if (F < 0 || T < 0) return fail(LDPC_EINVAL, "F and T must be >= 0");
     if (!(clip > 0.f)) return fail(LDPC_EINVAL, "clip must be positive");
     if (c->dc_max > kWMaxDeg) return fail(LDPC_ENOTSUP, "weighted BP supports row degree <= %d", kWMaxDeg);
+    if (c->dv_max > kWMaxCol) return fail(LDPC_ENOTSUP, "weighted BP supports column degree <= %d", kWMaxCol);
     if (ceil_div(F, kWFB) > 65535) return fail(LDPC_ENOTSUP, "too many frames (F=%d)", F);
     return LDPC_OK;
 }
