@@ -48,7 +48,7 @@ typedef enum {
     LDPC_ENOMEM = -2,   /* host or device allocation failed */
     LDPC_ECUDA = -3,    /* a CUDA call or kernel launch failed */
     LDPC_ETIMEOUT = -4, /* a bounded wait inside a kernel gave up */
-    LDPC_ENOTSUP = -5   /* valid request outside what this build supports */
+    LDPC_ENOTSUP = -5   /* valid request outside what the library supports */
 } ldpc_status;
 
 /* Optional quasi-cyclic description: an mb x nb base matrix of circulant
