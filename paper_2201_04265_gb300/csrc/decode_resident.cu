@@ -150,6 +150,13 @@ __device__ __forceinline__ void sts_u(uint32_t a, uint32_t v) {
 // NE message planes, then G planes of totals L, then (regular codes) G planes
 // of channel LLRs R.  Regular codes (three edges per bit) need three message
 // planes and keep R on chip, which frees the registers that would hold it.
+// Regular codes keep a row of 32 spare words right after the message planes:
+// a thread's unused check slots point there (slot NE P + lane), so every
+// thread runs all its check slots without a branch; such a dummy check reads
+// real totals (bits 0..31), writes only its spare word, and is left out of
+// every syndrome.
+constexpr uint32_t kDummyBytes = 128;
+
 template <bool REG, int NSL = kResSlots>
 struct Planes {
     static constexpr int NE = REG ? 3 : NSL;
@@ -176,10 +183,11 @@ struct Smem {
         else return pmask_;
     }
     __device__ uint32_t l0() const {
-        if constexpr (PL > 0) return e0 + NE * (4u << PL);
+        if constexpr (PL > 0) return e0 + NE * (4u << PL) + (REG ? kDummyBytes : 0);
         else return l0_;
     }
     __device__ uint32_t eaddr(uint32_t s) const { return e0 + 4u * s; }
+    __device__ uint32_t dummy_slot() const { return NE * (pmask() + 1u); }
     __device__ uint32_t laddr(uint32_t s, int i) const { return l0() + i * plane() + 4u * (s & pmask()); }
     __device__ uint32_t eb(int v, int r) const { return e0 + r * plane() + 4u * v; }
     __device__ uint32_t lb(int v, int i) const { return l0() + i * plane() + 4u * v; }
@@ -191,7 +199,7 @@ struct Smem {
 
 template <class MsgT, int G, bool REG, int NSL = kResSlots>
 __host__ __device__ __forceinline__ size_t group_bytes(int npad) {
-    return (size_t)(Planes<REG, NSL>::NE + G + (Planes<REG, NSL>::RSM ? G : 0)) * 4u * npad;
+    return (size_t)(Planes<REG, NSL>::NE + G + (Planes<REG, NSL>::RSM ? G : 0)) * 4u * npad + (REG ? kDummyBytes : 0);
 }
 
 __device__ __forceinline__ uint32_t slot_of(const uint32_t *w, int j) {
@@ -214,7 +222,7 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
     for (int i = 0; i < G; ++i) zacc[i] = 0;
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
-        if ((idx[k][0] & 0xFFFFu) == kNoSlot) continue;  // no check in this slot
+        if (!REG && (idx[k][0] & 0xFFFFu) == kNoSlot) continue;  // no check in this slot
         uint32_t slot[DC];
 #pragma unroll
         for (int j = 0; j < DC; ++j) slot[j] = slot_of(idx[k], j);
@@ -247,7 +255,8 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
         }
         // parity of z = [L >= 0] over the row = d + parity of [L < 0] (the bit
         // pass leaves no -0, so the sign bit is exactly [L < 0])
-        if (SYN)
+        const bool real = !REG || slot[0] < sm.dummy_slot();
+        if (SYN && real)
 #pragma unroll
             for (int i = 0; i < G; ++i) zacc[i] |= (zsgn[i] >> 31) ^ (uint32_t)(d & 1);
         // (-1)^d folded into the accumulated sign bit
@@ -290,7 +299,7 @@ __device__ __forceinline__ uint32_t syndrome_pass(const uint32_t (&idx)[CPT][(DC
 #pragma unroll
         for (int j = 0; j < DC; ++j) {
             const uint32_t s = slot_of(idx[k], j);
-            if (s == kNoSlot) continue;
+            if (s == kNoSlot || (REG && s >= sm.dummy_slot())) continue;
 #pragma unroll
             for (int i = 0; i < G; ++i) par ^= (uint32_t)(lds_f(sm.laddr(s, i)) >= 0.f) << i;
         }
@@ -479,7 +488,7 @@ __device__ __forceinline__ Smem<MsgT, G, REG, PL, NSL> smem_at(unsigned char *ba
     sm.e0 = (uint32_t)__cvta_generic_to_shared(base);
     sm.plane_ = 4u * (uint32_t)npad;
     sm.pmask_ = (uint32_t)npad - 1u;
-    sm.l0_ = sm.e0 + Planes<REG, NSL>::NE * sm.plane_;
+    sm.l0_ = sm.e0 + Planes<REG, NSL>::NE * sm.plane_ + (REG ? kDummyBytes : 0);
     return sm;
 }
 
@@ -591,7 +600,14 @@ std::vector<uint32_t> build_slot_table(const ldpc_code *c, int dc, int cpt, int 
     for (int32_t v = 0; v < c->n; ++v)
         for (int32_t q = c->col_ptr[v]; q < c->col_ptr[v + 1]; ++q)
             rank[c->col_edge[q]] = (uint32_t)(q - c->col_ptr[v]);
+    const bool reg = c->dc_min == dc && c->dc_max == dc && c->dv_min == 3 && c->dv_max == 3;
     std::vector<uint32_t> tab((size_t)cpt * DCW * T, 0xFFFFFFFFu);
+    if (reg)
+        for (size_t w = 0; w < (size_t)cpt * DCW; ++w)
+            for (int t = 0; t < T; ++t) {
+                const uint32_t d = 3u * (uint32_t)npad + (uint32_t)(t % 32);
+                tab[w * T + t] = d | (d << 16);
+            }
     const int ngroups = (int)(c->sched_groups.size() / 32);
     for (int g = 0; g < ngroups; ++g) {
         const int w = g % warps, k = g / warps;
