@@ -626,6 +626,32 @@ std::vector<uint32_t> build_slot_table(const ldpc_code *c, int dc, int cpt, int 
             }
         }
     }
+    // dummy checks of regular codes: at every step, on the spare word whose
+    // bank no real check of the warp touches at that step (spare word b sits in
+    // bank b, like bit b), so they add no bank conflict
+    if (reg)
+        for (int k = 0; k < cpt; ++k)
+            for (int w = 0; w < warps; ++w) {
+                const int g = k * warps + w;
+                for (int j = 0; j < dc; ++j) {
+                    uint32_t used = 0;
+                    for (int u = 0; u < 32; ++u) {
+                        const int32_t chk = g < ngroups ? c->sched_groups[(size_t)g * 32 + u] : -1;
+                        if (chk >= 0) used |= 1u << (c->col_idx[c->eval_edge[c->row_ptr[chk] + j]] & 31);
+                    }
+                    uint32_t b = 0;
+                    for (int u = 0; u < 32; ++u) {
+                        const int32_t chk = g < ngroups ? c->sched_groups[(size_t)g * 32 + u] : -1;
+                        if (chk >= 0) continue;
+                        while ((used >> b) & 1u) ++b;  // a free bank remains: at most 32 lanes
+                        const uint32_t slot = 3u * (uint32_t)npad + b;
+                        used |= 1u << b;
+                        uint32_t &word = tab[(size_t)(k * DCW + j / 2) * T + 32 * w + u];
+                        const int sh = (j & 1) * 16;
+                        word = (word & ~(0xFFFFu << sh)) | (slot << sh);
+                    }
+                }
+            }
     return tab;
 }
 
