@@ -122,7 +122,12 @@ int ldpc_syndrome(const ldpc_code *code, const uint32_t *d_bits, int32_t F, uint
 #define LDPC_SCHED_PLAIN 1    /* flooding, messages streamed through HBM,
                                  one check and one bit kernel per iteration */
 #define LDPC_SCHED_RESIDENT 2 /* persistent kernel, frames held in shared
-                                 memory for all iterations */
+                                 memory for all iterations: rows of up to 16
+                                 edges with columns of up to 4, or rows of
+                                 10-12 with columns of up to 9, and a frame
+                                 group that fits one SM (about n <= 8192
+                                 for binary16 messages); LDPC_ENOTSUP
+                                 otherwise */
 
 typedef struct {
     int32_t max_iters;  /* T >= 0 iterations (an iteration = all check
