@@ -491,7 +491,8 @@ def paper_table1(L, torch, dev):
     figure is the median of 5 timed repetitions after a warm-up."""
     import ldpc_synth as S
     out = {"vectors": 1000, "iterations": 10, "ebn0_db": 2.0, "unit": "us per vector",
-           "decoder": "schedule auto (resident where the code fits, else plain), FP32 messages",
+           "decoder": "schedule auto (resident where the code fits, else plain; one vector takes the "
+                      "small-batch plan), FP32 messages",
            "single": "one vector per call: encode or decode latency in us"}
     for rate in (0.25, 0.5, 0.75):
         h = S.table1_code(rate, seed=6)
@@ -560,6 +561,19 @@ def run_profile_case(args):
     import ldpc_synth as S
     import paper_2201_04265_gb300 as L
     torch.cuda.set_device(0)
+    if args.profile_case == "table1-vector":
+        # one vector of the Table I codes of rates 1/4 and 3/4, 10 iterations,
+        # FP32 messages, twice each: the latency path (small-batch plan)
+        for rate in (0.25, 0.75):
+            code = L.Code.from_csr_code(S.table1_code(rate, seed=6))
+            g = torch.Generator(device="cuda")
+            g.manual_seed(0)
+            llr = (torch.randn((1, code.n), device="cuda", generator=g) * 2.0 + 3.0).contiguous()
+            for _ in range(2):
+                r = L.decode(code, llr, max_iters=10, early_stop=False, want_post=False)
+            torch.cuda.synchronize()
+            print(json.dumps({"profile_case": args.profile_case, "rate": rate, "ok": int(r.ok.sum())}))
+        return
     if args.code == "qc":  # quasi-cyclic 46 x 68 base, 316 nonzeros, Z = 384 (n = 26112)
         code = L.Code.from_qc(S.qc_base_matrix(46, 68, 316, 3, 19, 384, seed=3), 384)
     else:
@@ -586,7 +600,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-table1", action="store_true", help="skip the paper's Table I workload")
     ap.add_argument("--ref-frames-per-thread", type=int, default=4)
-    ap.add_argument("--profile-case", choices=["resident", "plain"], default=None,
+    ap.add_argument("--profile-case", choices=["resident", "plain", "table1-vector"], default=None,
                     help="run one small decode (for ncu captures) instead of the benchmark")
     ap.add_argument("--frames", type=int, default=4096, help="frames of the --profile-case run")
     ap.add_argument("--fp16", action="store_true", help="binary16 messages in the plain --profile-case run")

@@ -208,7 +208,7 @@ int upload(T **dst, const T *src, size_t count) {
 
 void free_device(ldpc_code *c) {
     void *ptrs[] = {c->d.row_ptr,   c->d.col_idx,    c->d.col_ptr,  c->d.col_edge,
-                    c->d.info_pos,  c->d.parity_pos, c->d.AT,       c->d.res_edges,
+                    c->d.info_pos,  c->d.parity_pos, c->d.AT,       c->d.res_edges,  c->d.lat_edges,
                     c->d.eval_col,  c->d.eval_edge,  c->d.col_pos,  c->d.row_order,
                     c->d.col_order};
     for (void *p : ptrs)
@@ -240,6 +240,8 @@ int upload_code(ldpc_code *c) {
     if (c->res.ok) {
         LDPC_TRY(upload(&c->d.res_edges, c->res.edges.data(), c->res.edges.size()));
         c->d.res_edges_len = (int32_t)c->res.edges.size();
+        if (c->res.lat_threads > 0)
+            LDPC_TRY(upload(&c->d.lat_edges, c->res.lat_edges.data(), c->res.lat_edges.size()));
     }
     c->on_device = true;
     return LDPC_OK;

@@ -118,7 +118,7 @@ struct ResArgs {
     uint32_t *hard;
     int32_t *iters;
     uint8_t *ok;
-    unsigned *counter;
+    unsigned *counter;      // work counter, or null: CTA b decodes group b
 };
 
 // 32-bit shared-memory accesses (addresses in the shared window).  Stores
@@ -506,11 +506,17 @@ resident_kernel(ResArgs a) {
 #pragma unroll
         for (int w = 0; w < DCW; ++w) idx[k][w] = __ldg(&a.edges[(size_t)(k * DCW + w) * T + tid]);
     const int groups = (a.F + G - 1) / G;
-    for (;;) {
-        if (tid == 0) s_group = (int)atomicAdd(a.counter, 1u);
-        __syncthreads();
-        const int grp = s_group;
-        __syncthreads();
+    for (int pass = 0;; ++pass) {
+        int grp;
+        if (a.counter) {  // groups taken from the work counter
+            if (tid == 0) s_group = (int)atomicAdd(a.counter, 1u);
+            __syncthreads();
+            grp = s_group;
+            __syncthreads();
+        } else {  // one group per CTA (grid = groups)
+            if (pass > 0) break;
+            grp = blockIdx.x;
+        }
         if (grp >= groups) break;
         ResIO<G> io;
 #pragma unroll
@@ -591,8 +597,11 @@ int res_slots(const ldpc_code *c) {
 // g mod (T/32), check slot g / (T/32); lane u takes the group's u-th check,
 // whose slots are listed in evaluation order.  The slot of an edge is r P + v,
 // v its bit and r the edge's rank in v's column (ascending CSR edge order).
-// Returns an empty table if the schedule needs more slots than CPT.
-std::vector<uint32_t> build_slot_table(const ldpc_code *c, int dc, int cpt, int T) {
+// Returns an empty table if the schedule needs more slots than CPT.  With
+// `dummies` (the regular-code kernels), unused check slots of a regular code
+// get dummy checks; otherwise they stay empty (kNoSlot), for the general
+// kernels.
+std::vector<uint32_t> build_slot_table(const ldpc_code *c, int dc, int cpt, int T, bool dummies = true) {
     const int DCW = (dc + 1) / 2;
     const int npad = pad_bits(c);
     const int warps = T / 32;
@@ -600,7 +609,7 @@ std::vector<uint32_t> build_slot_table(const ldpc_code *c, int dc, int cpt, int 
     for (int32_t v = 0; v < c->n; ++v)
         for (int32_t q = c->col_ptr[v]; q < c->col_ptr[v + 1]; ++q)
             rank[c->col_edge[q]] = (uint32_t)(q - c->col_ptr[v]);
-    const bool reg = c->dc_min == dc && c->dc_max == dc && c->dv_min == 3 && c->dv_max == 3;
+    const bool reg = dummies && c->dc_min == dc && c->dc_max == dc && c->dv_min == 3 && c->dv_max == 3;
     std::vector<uint32_t> tab((size_t)cpt * DCW * T, 0xFFFFFFFFu);
     if (reg)
         for (size_t w = 0; w < (size_t)cpt * DCW; ++w)
@@ -702,6 +711,22 @@ int build_resident_plan(ldpc_code *c) {
     // exactly dc edges per check and three per bit: the specialised kernels
     p.regular = c->dc_min == shape->dc && c->dc_max == shape->dc && c->dv_min == 3 && c->dv_max == 3;
     p.ok = true;
+    // Small-batch plan: when there are fewer frames than SMs, each CTA has the
+    // SM to itself, so the same schedule groups are spread over as many warps
+    // as a CTA holds (at most 16), cutting the checks each thread runs in
+    // sequence -- the critical path of an iteration -- from cpt to
+    // ceil(groups / 16).  It runs the general (non-regular) kernel with empty
+    // check slots skipped.  Every check keeps its evaluation order and every
+    // bit its summation order, so the results are the same bits.
+    const int ngroups = (int)(c->sched_groups.size() / 32);
+    const int warps_max = kResMaxThreads / 32;
+    const int per_thread = (int)ceil_div(ngroups, warps_max);
+    const int warps = (int)ceil_div(ngroups, std::max(per_thread, 1));
+    const int Tl = 32 * warps;
+    if (ngroups > 0 && per_thread < shape->cpt && (int64_t)Tl * kResVPT >= c->n) {
+        p.lat_edges = build_slot_table(c, shape->dc, shape->cpt, Tl, false);
+        if (!p.lat_edges.empty()) p.lat_threads = Tl;
+    }
     return LDPC_OK;
 }
 
@@ -731,10 +756,22 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
         fn = fp16 ? pick_kernel<__half, 2>(c->res.dc_pad, c->res.regular, syn)
                   : pick_kernel<float, 1>(c->res.dc_pad, c->res.regular, syn);
     if (!fn) return fail(LDPC_ENOTSUP, "no resident kernel for row degree %d", c->res.dc_pad);
-    const int T = c->res.rows_pad;
-    const size_t smem = res_smem(c, fp16, c->res.regular, c->res.dv_pad);
     int sms = 0, per_sm = 0;
     LDPC_TRY(sm_count(&sms));
+    int T = c->res.rows_pad;
+    bool reg = c->res.regular;
+    const uint32_t *edges = c->d.res_edges;
+    if (!fp16 && c->res.lat_threads > 0 && F <= sms) {  // the small-batch plan
+        reg = false;
+        T = c->res.lat_threads;
+        edges = c->d.lat_edges;
+        fn = c->res.dv_pad == kResSlotsWide
+                 ? (syn ? resident_kernel<float, 1, 12, 4, false, true, 0, kResSlotsWide>
+                        : resident_kernel<float, 1, 12, 4, false, false, 0, kResSlotsWide>)
+                 : pick_kernel<float, 1>(c->res.dc_pad, false, syn);
+        if (!fn) return fail(LDPC_ENOTSUP, "no resident kernel for row degree %d", c->res.dc_pad);
+    }
+    const size_t smem = res_smem(c, fp16, reg, c->res.dv_pad);
     LDPC_TRY(kernel_setup((const void *)fn, T, smem, &per_sm));
     if (per_sm < 1) return fail(LDPC_ENOTSUP, "resident kernel cannot be resident (smem %zu B)", smem);
     const int G = fp16 ? 2 : 1;
@@ -750,13 +787,15 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
     a.T_iters = o->max_iters;
     a.early_stop = o->early_stop;
     a.clip2 = clip_log2(o->clip);
-    a.edges = c->d.res_edges;
+    a.edges = edges;
     a.post = d_post;
     a.hard = d_hard;
     a.iters = d_iters;
     a.ok = d_ok;
-    a.counter = static_cast<unsigned *>(d_work);
-    LDPC_TRY_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned), s));
+    // a grid with a CTA per group needs no work counter (nor its memset: one
+    // launch fewer on the latency path)
+    a.counter = grid < groups ? static_cast<unsigned *>(d_work) : nullptr;
+    if (a.counter) LDPC_TRY_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned), s));
     fn<<<grid, T, smem, s>>>(a);
     LDPC_TRY_CUDA(cudaGetLastError());
     return LDPC_OK;

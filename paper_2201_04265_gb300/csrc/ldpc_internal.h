@@ -68,6 +68,7 @@ struct DeviceCode {
     // resident decoder tables (see decode_resident.cu)
     uint32_t *res_edges = nullptr; // resident slot table of the single-code launch
     int32_t res_edges_len = 0;
+    uint32_t *lat_edges = nullptr; // slot table of the small-batch (latency) launch
 };
 
 // Resident-decoder plan: how one frame's checks and bits are laid out in
@@ -78,6 +79,8 @@ struct ResidentPlan {
     int32_t dc_pad = 0;       // row degree padded to an instantiated shape
     int32_t dv_pad = 0;       // message slots per bit (16-byte records)
     int32_t rows_pad = 0;     // threads per CTA of the resident launch
+    int32_t lat_threads = 0;  // threads per CTA of the small-batch launch, 0 = none
+    std::vector<uint32_t> lat_edges;  // its slot table, same form as `edges`
     std::vector<uint32_t> edges; // [cpt * ceil(dc_pad/2)][threads] 16-bit slot pairs
 };
 

@@ -40,6 +40,8 @@ CODES = {
     "irregular_37x70": lambda: S.dense_to_code(
         np.random.default_rng(5).integers(0, 2, (37, 70), dtype=np.uint8)),
     "qc_small": lambda: S.qc_expand(S.qc_base_matrix(8, 12, 40, 3, 8, 24, seed=3), 24),
+    # irregular (rows of 3..7 ones, columns of 1..4) and small enough to decode on chip
+    "qc_irregular_512": lambda: S.qc_expand(S.qc_base_matrix(8, 16, 40, 3, 8, 32, seed=2), 32),
     "c2_random_8064": lambda: S.random_regular(8064, 3, 6, seed=2),
 }
 

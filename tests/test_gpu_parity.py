@@ -123,8 +123,8 @@ def test_decode_fp32_few_iterations_all_frames(L, name, T):
 @pytest.mark.parametrize("name", ["table1_r025", "table1_r050", "table1_r075"])
 def test_decode_table1_paper_setting(L, name):
     """The paper's Table I workload (n = 1032, 12 ones per row, 9/6/3 per
-    column, 10 fixed iterations) through the default schedule: the plain
-    decoder for column weights 9 and 6, the resident one for 3."""
+    column, 10 fixed iterations) through the default schedule, which decodes
+    all three codes on chip (nine message planes for column weights 9 and 6)."""
     w = workload(name, 200, 3.0, seed=31)
     c = dev_code(L, name)
     post, hard, iters, ok = _gpu_decode(L, c, w.llr, max_iters=10)
@@ -249,6 +249,33 @@ def test_resident_matches_plain_bit_for_bit(L, name, fp16, early_stop):
     b = _gpu_decode(L, c, w.llr, schedule="resident", **kw)
     for x, y in zip(a, b):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("name", ["c1_gallager_504", "reg312_2016", "qc_irregular_512",
+                                  "table1_r025", "table1_r050", "table1_r075"])
+@pytest.mark.parametrize("F", [1, 37])
+@pytest.mark.parametrize("early_stop", [False, True])
+def test_resident_small_batch_plan_bit_for_bit(L, name, F, early_stop):
+    """With FP32 messages and no more frames than SMs the resident decoder
+    spreads each frame's checks over more threads (the small-batch plan).
+    Check and bit arithmetic keep their order, so it must agree exactly with
+    the plain decoder, and each frame's result must not depend on the batch it
+    came in (a batch larger than the SM count takes the throughput plan)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    w = workload(name, F, 2.0, seed=83)
+    c = dev_code(L, name)
+    kw = dict(max_iters=15, early_stop=early_stop)
+    try:
+        b = _gpu_decode(L, c, w.llr, schedule="resident", **kw)
+    except L.LdpcError:
+        pytest.skip("code has no resident layout")
+    a = _gpu_decode(L, c, w.llr, schedule="plain", **kw)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    big = np.concatenate([w.llr] * (sms // F + 1))[: sms + 5]
+    d = _gpu_decode(L, c, big, schedule="resident", **kw)
+    for x, y in zip(b, d):
+        np.testing.assert_array_equal(x, y[:F])
 
 
 def test_resident_against_oracle(L):
