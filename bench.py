@@ -493,7 +493,9 @@ def paper_table1(L, torch, dev):
     out = {"vectors": 1000, "iterations": 10, "ebn0_db": 2.0, "unit": "us per vector",
            "decoder": "schedule auto (resident where the code fits, else plain; one vector takes the "
                       "small-batch plan), FP32 messages",
-           "single": "one vector per call: encode or decode latency in us"}
+           "single": "one vector per call: encode or decode latency in us (decode_single_graph: "
+                     "replayed from a CUDA graph; decode_single_graph_0_iters: the same call with "
+                     "0 iterations, its fixed part)"}
     for rate in (0.25, 0.5, 0.75):
         h = S.table1_code(rate, seed=6)
         code = L.Code.from_csr_code(h)
@@ -543,11 +545,20 @@ def paper_table1(L, torch, dev):
         with torch.cuda.graph(graph):
             L.decode(code, llr1, out=r1, workspace=ws1, **kw)
         dec_1g = timed(graph.replay)
+        # the same call with 0 iterations (load, hard decisions, syndrome,
+        # outputs): the fixed part of the one-vector latency
+        with torch.cuda.stream(side):
+            L.decode(code, llr1, out=r1, workspace=ws1, **dict(kw, max_iters=0))
+        torch.cuda.current_stream().wait_stream(side)
+        graph0 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph0):
+            L.decode(code, llr1, out=r1, workspace=ws1, **dict(kw, max_iters=0))
+        dec_1g0 = timed(graph0.replay)
         ok = float(r.ok.float().mean())
         out[f"rate_{rate}"] = {"m": code.m, "k": code.k, "encode_batch": round(enc_b, 4),
                                "decode_batch": round(dec_b, 4), "encode_single": round(enc_1, 2),
                                "decode_single": round(dec_1, 2), "decode_single_graph": round(dec_1g, 2),
-                               "frames_ok": ok}
+                               "decode_single_graph_0_iters": round(dec_1g0, 2), "frames_ok": ok}
         code.close()
     return out
 

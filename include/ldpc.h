@@ -127,7 +127,9 @@ int ldpc_syndrome(const ldpc_code *code, const uint32_t *d_bits, int32_t F, uint
                                  10-12 with columns of up to 9, and a frame
                                  group that fits one SM (about n <= 8192
                                  for binary16 messages); LDPC_ENOTSUP
-                                 otherwise */
+                                 otherwise.  With FP32 messages and no more
+                                 frames than SMs, each frame gets more
+                                 threads (lower latency, same bits) */
 
 typedef struct {
     int32_t max_iters;  /* T >= 0 iterations (an iteration = all check

@@ -118,7 +118,7 @@ struct ResArgs {
     uint32_t *hard;
     int32_t *iters;
     uint8_t *ok;
-    unsigned *counter;      // work counter, or null: CTA b decodes group b
+    unsigned *counter;
 };
 
 // 32-bit shared-memory accesses (addresses in the shared window).  Stores
@@ -506,17 +506,11 @@ resident_kernel(ResArgs a) {
 #pragma unroll
         for (int w = 0; w < DCW; ++w) idx[k][w] = __ldg(&a.edges[(size_t)(k * DCW + w) * T + tid]);
     const int groups = (a.F + G - 1) / G;
-    for (int pass = 0;; ++pass) {
-        int grp;
-        if (a.counter) {  // groups taken from the work counter
-            if (tid == 0) s_group = (int)atomicAdd(a.counter, 1u);
-            __syncthreads();
-            grp = s_group;
-            __syncthreads();
-        } else {  // one group per CTA (grid = groups)
-            if (pass > 0) break;
-            grp = blockIdx.x;
-        }
+    for (;;) {
+        if (tid == 0) s_group = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int grp = s_group;
+        __syncthreads();
         if (grp >= groups) break;
         ResIO<G> io;
 #pragma unroll
@@ -792,10 +786,8 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
     a.hard = d_hard;
     a.iters = d_iters;
     a.ok = d_ok;
-    // a grid with a CTA per group needs no work counter (nor its memset: one
-    // launch fewer on the latency path)
-    a.counter = grid < groups ? static_cast<unsigned *>(d_work) : nullptr;
-    if (a.counter) LDPC_TRY_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned), s));
+    a.counter = static_cast<unsigned *>(d_work);
+    LDPC_TRY_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned), s));
     fn<<<grid, T, smem, s>>>(a);
     LDPC_TRY_CUDA(cudaGetLastError());
     return LDPC_OK;
