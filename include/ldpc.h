@@ -111,6 +111,24 @@ void ldpc_code_destroy(ldpc_code *code);
 int ldpc_encode(const ldpc_code *code, const uint32_t *d_info, uint32_t *d_code, int32_t F,
                 ldpc_stream_t stream);
 
+/* Four-Russians encoding tables (no counterpart in the paper, which states
+ * only the product of Eq. 3).  For each group of 8 information bits and each
+ * of the 256 byte values, the XOR of the selected columns of A, so that the
+ * parity of a frame is one table row per group and 128 parity bits instead
+ * of AND/XOR steps over every word of every row of A.  Builds the tables on
+ * the code's device (synchronous; 4 KB per 128 parity bits per 8 information
+ * bits: 66 MB for n = 8064 at rate 1/2, 600 MB for n = 26112 at rate 1/3);
+ * from then on ldpc_encode uses them, with the same result bits.  *bytes
+ * (may be NULL) receives the device memory held (0 when k or rank is 0:
+ * nothing to look up, no tables).  Rebuilding replaces the tables.
+ * Errors: LDPC_EINVAL (host-only code, wrong device), LDPC_ENOTSUP when
+ * 4 ceil(rank/128) > ceil(n/32) (the lookup uses each codeword row as
+ * scratch), LDPC_ENOMEM, LDPC_ECUDA.  Must not race with ldpc_encode calls
+ * on the same code (synchronise first); so must ldpc_encode_tables_free,
+ * which returns ldpc_encode to the AND/XOR form. */
+int ldpc_encode_tables_build(ldpc_code *code, size_t *bytes);
+int ldpc_encode_tables_free(ldpc_code *code);
+
 /* Syndrome s = H z^T over GF(2) (Eq. 1) of F packed words d_bits (F x NW).
  * d_syn (F x ceil(m/32) words, bit c = check c) and d_ok (F bytes, 1 when
  * every check is satisfied) may each be NULL. */

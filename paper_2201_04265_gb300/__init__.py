@@ -17,7 +17,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DecodeOpts, LdpcError, QcDesc, c_i32, c_i64, c_vp
+from ._lib import DecodeOpts, LdpcError, QcDesc, c_i32, c_i64, c_size, c_vp
 
 SCHED_AUTO, SCHED_PLAIN, SCHED_RESIDENT = 0, 1, 2
 _SCHED = {"auto": SCHED_AUTO, "plain": SCHED_PLAIN, "resident": SCHED_RESIDENT}
@@ -112,6 +112,18 @@ class Code:
         a = np.zeros((max(self.rank, 1), self.KW), dtype=np.uint32)
         _lib.check(self._lib.ldpc_code_parity_map(self.handle, c_vp(a.ctypes.data)), "ldpc_code_parity_map")
         return a[:self.rank]
+
+    def build_encode_tables(self) -> int:
+        """Builds the Four-Russians encoding tables on the device (synchronous);
+        `encode` uses them from then on, with the same result bits.  Returns
+        the device bytes they hold."""
+        nbytes = c_size()
+        _lib.check(self._lib.ldpc_encode_tables_build(self.handle, ctypes.byref(nbytes)),
+                   "ldpc_encode_tables_build")
+        return nbytes.value
+
+    def free_encode_tables(self) -> None:
+        _lib.check(self._lib.ldpc_encode_tables_free(self.handle), "ldpc_encode_tables_free")
 
     def schedule(self) -> tuple[np.ndarray, int]:
         """(evaluation order as CSR edge ids per row, edges not placed conflict-free)."""

@@ -52,6 +52,8 @@ SIGNATURES = {
     "ldpc_code_schedule": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i64)]),
     "ldpc_code_destroy": (None, [c_vp]),
     "ldpc_encode": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp]),
+    "ldpc_encode_tables_build": (c_i32, [c_vp, ctypes.POINTER(c_size)]),
+    "ldpc_encode_tables_free": (c_i32, [c_vp]),
     "ldpc_syndrome": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "ldpc_decode_workspace_size": (c_i32, [c_vp, c_i32, ctypes.POINTER(DecodeOpts),
                                            ctypes.POINTER(c_size)]),

@@ -98,6 +98,17 @@ int ldpc_encode(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, in
     return launch_encode(c, d_info, d_code, F, (cudaStream_t)stream);
 }
 
+int ldpc_encode_tables_build(ldpc_code *c, size_t *bytes) {
+    LDPC_TRY(check_code(c));
+    return build_encode_tables(c, bytes);
+}
+
+int ldpc_encode_tables_free(ldpc_code *c) {
+    LDPC_TRY(check_code(c));
+    free_encode_tables(c);
+    return LDPC_OK;
+}
+
 int ldpc_syndrome(const ldpc_code *c, const uint32_t *d_bits, int32_t F, uint32_t *d_syn,
                   uint8_t *d_ok, ldpc_stream_t stream) {
     LDPC_TRY(check_code(c));

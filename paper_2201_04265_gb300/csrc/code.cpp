@@ -210,7 +210,7 @@ void free_device(ldpc_code *c) {
     void *ptrs[] = {c->d.row_ptr,   c->d.col_idx,    c->d.col_ptr,  c->d.col_edge,
                     c->d.info_pos,  c->d.parity_pos, c->d.AT,       c->d.res_edges,  c->d.lat_edges,
                     c->d.eval_col,  c->d.eval_edge,  c->d.col_pos,  c->d.row_order,
-                    c->d.col_order};
+                    c->d.col_order, c->d.enc_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->d = DeviceCode{};

@@ -69,6 +69,11 @@ struct DeviceCode {
     uint32_t *res_edges = nullptr; // resident slot table of the single-code launch
     int32_t res_edges_len = 0;
     uint32_t *lat_edges = nullptr; // slot table of the small-batch (latency) launch
+    // Four-Russians encoding tables (encode.cu), built on request:
+    // [enc_ns][enc_ng][256][4] words, 0 = not built
+    uint32_t *enc_tab = nullptr;
+    int32_t enc_ns = 0, enc_ng = 0;
+    size_t enc_tab_bytes = 0;
 };
 
 // Resident-decoder plan: how one frame's checks and bits are laid out in
@@ -118,6 +123,8 @@ int resident_group_slots(const ldpc_code *c);       // decode_resident.cu
 int kernel_setup(const void *fn, int threads, size_t smem, int *per_sm);
 int sm_count(int *sms);
 // Kernel launchers (defined in the .cu files).
+int build_encode_tables(ldpc_code *c, size_t *bytes);
+void free_encode_tables(ldpc_code *c);
 int launch_encode(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, int32_t F,
                   cudaStream_t s);
 int launch_syndrome(const ldpc_code *c, const uint32_t *d_bits, int32_t F, uint32_t *d_syn,

@@ -76,6 +76,22 @@ def test_c2_encode_full_batch(L, c2):
     assert bool(ok.all())
 
 
+def test_c2_encode_full_batch_tables(L, c2):
+    """The whole 65536-frame batch through the Four-Russians tables: the same
+    codewords as the AND/XOR form, and the oracle's on the sampled frames."""
+    h, sysm, code, cw, _, sample, rate = c2
+    info = torch.from_numpy(_pack(S.info_bits(F2, sysm.k, SEED2)).view(np.int32)).cuda()
+    code.build_encode_tables()
+    try:
+        words = L.encode(code, info)
+    finally:
+        code.free_encode_tables()
+    got = _unpack(words.cpu().numpy().view(np.uint32), h.n)
+    np.testing.assert_array_equal(got, cw)
+    want, _ = _oracle_frames(h, sysm, rate, sample)
+    np.testing.assert_array_equal(got[sample], want)
+
+
 @pytest.mark.parametrize("fp16", [False, True])
 def test_c2_decode_full_batch_sampled_frames(L, c2, fp16):
     h, sysm, code, cw, llr, sample, rate = c2
@@ -117,6 +133,29 @@ def test_qc_encode_full_batch_properties(L, qc):
     info_pos, _ = code.positions()
     np.testing.assert_array_equal(bits[:, info_pos], info[:64])   # systematic
     assert not oracle.syndrome(h, bits).any()               # checked by the oracle too
+
+
+def test_qc_encode_full_batch_tables(L, qc):
+    """4096 frames of the n = 26112 code through the Four-Russians tables
+    (about 600 MB): same codewords as the AND/XOR form, all satisfy H c^T = 0,
+    and the oracle's syndrome agrees on a sample."""
+    h, code = qc
+    F = 4096
+    info_bits = S.info_bits(F, code.k, 7301)
+    info = torch.from_numpy(S.pack_bits(info_bits).view(np.int32)).cuda()
+    ref = L.encode(code, info)
+    code.build_encode_tables()
+    try:
+        words = L.encode(code, info)
+    finally:
+        code.free_encode_tables()
+    assert torch.equal(words, ref)
+    _, ok = L.syndrome(code, words, want_syn=False)
+    assert bool(ok.all())
+    bits = S.unpack_bits(words.cpu().numpy()[:32].view(np.uint32), code.n)
+    info_pos, _ = code.positions()
+    np.testing.assert_array_equal(bits[:, info_pos], info_bits[:32])
+    assert not oracle.syndrome(h, bits).any()
 
 
 def test_qc_decode_full_batch_sampled_frames(L, qc):

@@ -63,6 +63,43 @@ def test_encode_bit_exact(L, name, F):
         assert not (raw[:, -1] >> np.uint32(code.n % 32)).any()
 
 
+@pytest.mark.parametrize("name", ["c1_gallager_504", "qc_small", "qc_irregular_512", "table1_r025",
+                                  "table1_r075", "reg312_2016"])
+@pytest.mark.parametrize("F", [1, 33, 300])
+def test_encode_tables_bit_exact(L, name, F):
+    """Four-Russians tables: the oracle's codewords, whatever the bits beyond k
+    in the last information word; freeing the tables returns to the AND/XOR
+    form with the same result."""
+    code, sysm = code_and_sys(name)
+    c = L.Code.from_csr_code(code)   # its own object: the tables change its encode path
+    msgs = S.info_bits(F, sysm.k, seed=400 + F)
+    want = oracle.encode(sysm, msgs)
+    info = to_dev_words(msgs)
+    if sysm.k % 32:   # garbage in the pad bits of the last word
+        junk = np.random.default_rng(F).integers(0, 2 ** 31, F).astype(np.int32) << (sysm.k % 32)
+        info[:, -1] |= torch.from_numpy(junk).cuda()
+    nbytes = c.build_encode_tables()
+    assert nbytes == 4096 * (-(-(-(-c.rank // 32)) // 4)) * (-(-c.k // 8))
+    got = from_dev_words(L.encode(c, info), code.n)
+    np.testing.assert_array_equal(got, want)
+    c.free_encode_tables()
+    np.testing.assert_array_equal(from_dev_words(L.encode(c, info), code.n), want)
+    c.close()
+
+
+def test_encode_tables_rejected_when_scratch_does_not_fit(L):
+    """A 70-bit code has 3 words per codeword, fewer than the 4 scratch words
+    of one parity slice: no tables, and encoding keeps the AND/XOR form."""
+    code, sysm = code_and_sys("irregular_37x70")
+    c = L.Code.from_csr_code(code)
+    with pytest.raises(L.LdpcError):
+        c.build_encode_tables()
+    msgs = S.info_bits(9, sysm.k, seed=5)
+    np.testing.assert_array_equal(from_dev_words(L.encode(c, to_dev_words(msgs)), code.n),
+                                  oracle.encode(sysm, msgs))
+    c.close()
+
+
 def test_encode_fig2_worked_example(L):
     g = read_golden("fig2_encoding.txt")
     c = L.Code.from_csr_code(S.fig2_code())
