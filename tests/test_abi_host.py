@@ -106,6 +106,11 @@ def test_host_only_code_cannot_decode(L):
     st = c._lib.ldpc_encode(c.handle, None, None, 1, None)
     assert st == -1
     assert b"host-only" in c._lib.ldpc_last_error()
+    # so do the encoder-table calls (no device memory is touched)
+    with pytest.raises(L.LdpcError, match="host-only"):
+        c.build_encode_tables()
+    with pytest.raises(L.LdpcError, match="host-only"):
+        c.free_encode_tables()
     del torch
 
 
