@@ -7,6 +7,7 @@ takes a value from the CUDA path.
 from __future__ import annotations
 
 import functools
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -71,17 +72,88 @@ def hard_close(gpu_hard: np.ndarray, ora_hard: np.ndarray, ora_post: np.ndarray)
     return (gpu_hard == ora_hard) | (np.abs(ora_post) < HARD_EPS)
 
 
-def fp32_conditioned_frames(code, llr, iters, early_stop=False, seed=0):
+def _dev_in_tol(post, ref_post) -> np.ndarray:
+    """Per frame: max over bits of |clip(post) - clip(ref)| in units of the tolerance."""
+    g = np.clip(np.asarray(post, dtype=np.float64), -CLIP, CLIP)
+    o = np.clip(ref_post, -CLIP, CLIP)
+    return np.max(np.abs(g - o) / np.maximum(ATOL, RTOL * np.abs(o)), axis=1)
+
+
+def _perturbed(llr, seed):
+    rng = np.random.default_rng(seed)
+    return llr.astype(np.float64) * (1.0 + rng.choice([-1.0, 1.0], size=llr.shape) * 2.0 ** -23)
+
+
+def fp32_conditioned_frames(code, llr, iters, early_stop=False, seed=0, nthreads=1):
     """Frames whose FP64 decode is stable under an FP32-rounding-sized input
     perturbation (relative 2^-23 per LLR): on those, FP32 arithmetic is expected
     to stay within tolerance; on the others BP itself amplifies rounding beyond
     it, so no single-precision decoder can be held to the FP64 values."""
-    rng = np.random.default_rng(seed)
-    pert = llr.astype(np.float64) * (1.0 + rng.choice([-1.0, 1.0], size=llr.shape) * 2.0 ** -23)
-    a = oracle.decode(code, llr, iters=iters, early_stop=early_stop)
-    b = oracle.decode(code, pert, iters=iters, early_stop=early_stop)
-    g = np.clip(b.post, -CLIP, CLIP)
-    o = np.clip(a.post, -CLIP, CLIP)
-    stable = np.all(np.abs(g - o) <= 0.1 * np.maximum(ATOL, RTOL * np.abs(o)), axis=1)
-    stable &= (a.iters == b.iters)
+    a = oracle.decode(code, llr, iters=iters, early_stop=early_stop, nthreads=nthreads)
+    b = oracle.decode(code, _perturbed(llr, seed), iters=iters, early_stop=early_stop, nthreads=nthreads)
+    stable = (_dev_in_tol(b.post, a.post) <= 0.1) & (a.iters == b.iters)
     return stable, a
+
+
+# Excluded (FP32-unconditioned) frames are still held to the FP64 decoder's own
+# sensitivity: the GPU posterior may differ from the FP64 one by at most
+# SPREAD_FACTOR times the largest difference that NPERTURB input perturbations
+# of one FP32 rounding produce in the FP64 decode (or by the tolerance itself).
+# Measured on GB300: the ratio was at most 1.9 over the excluded frames of the
+# n = 504 and n = 1032 codes at 20 and 50 iterations.
+SPREAD_FACTOR = 4.0
+NPERTURB = 3
+
+
+@dataclass
+class ParityReport:
+    frames: int
+    excluded: int            # FP32-unconditioned frames
+    max_dev_stable: float    # in tolerance units (<= 1 required)
+    max_ratio_excluded: float  # GPU deviation / FP64 perturbation spread (<= SPREAD_FACTOR)
+
+    @property
+    def excluded_frac(self) -> float:
+        return self.excluded / max(self.frames, 1)
+
+
+ORACLE_THREADS = min(16, os.cpu_count() or 1)
+
+
+def assert_fp32_parity(code, llr, iters, post, hard, gpu_iters, ok, early_stop=False,
+                       max_excluded=0.05, nthreads=ORACLE_THREADS) -> ParityReport:
+    """The FP32 parity gate of every decoder test (Eqs. 5-8 against the FP64
+    oracle):
+
+    * frames stable under an FP32-sized input perturbation: posteriors within
+      1e-4 relative or 1e-3 absolute (both clipped to +-20), hard decisions
+      identical except where the oracle's |L| < 1e-3, equal ok flags and equal
+      iteration counts;
+    * the other frames may make up at most ``max_excluded`` of the batch, and
+      each must lie within SPREAD_FACTOR times the FP64 decode's own spread
+      under NPERTURB such perturbations.
+    """
+    F = llr.shape[0]
+    base = oracle.decode(code, llr, iters=iters, early_stop=early_stop, nthreads=nthreads)
+    spread = np.zeros(F)
+    stable = np.ones(F, dtype=bool)
+    for k in range(NPERTURB):
+        b = oracle.decode(code, _perturbed(llr, k), iters=iters, early_stop=early_stop, nthreads=nthreads)
+        d = _dev_in_tol(b.post, base.post)
+        if k == 0:
+            stable = (d <= 0.1) & (b.iters == base.iters)
+        spread = np.maximum(spread, d)
+    dev = _dev_in_tol(post, base.post)
+    ex = ~stable
+    rep = ParityReport(frames=F, excluded=int(ex.sum()),
+                       max_dev_stable=float(dev[stable].max()) if stable.any() else 0.0,
+                       max_ratio_excluded=float(np.max(np.where(dev[ex] <= 1.0, 0.0, dev[ex] / spread[ex])))
+                       if ex.any() else 0.0)
+    if max_excluded is not None:
+        assert rep.excluded_frac <= max_excluded, (rep, "too many FP32-unconditioned frames")
+    assert rep.max_dev_stable <= 1.0, (rep, np.nonzero(stable & (dev > 1.0)))
+    assert hard_close(hard[stable], base.hard[stable], base.post[stable]).all()
+    np.testing.assert_array_equal(ok[stable], base.ok[stable])
+    np.testing.assert_array_equal(gpu_iters[stable], base.iters[stable])
+    assert rep.max_ratio_excluded <= SPREAD_FACTOR, (rep, "excluded frame outside the FP64 spread")
+    return rep

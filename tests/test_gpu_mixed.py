@@ -8,6 +8,7 @@ import torch
 
 import ldpc_synth as S
 import oracle
+from parity_util import assert_fp32_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -37,10 +38,11 @@ def mixed(L):
     return hs, syss, codes
 
 
-def _batch(mixed, F, seed):
+def _batch(mixed, F, seed, fc=None):
     hs, syss, _ = mixed
     rng = np.random.default_rng(seed)
-    fc = rng.integers(0, len(hs), F).astype(np.int32)
+    if fc is None:
+        fc = rng.integers(0, len(hs), F).astype(np.int32)
     ebn0 = rng.uniform(1.0, 4.0, F)
     llrs = []
     for f in range(F):
@@ -129,3 +131,32 @@ def test_mixed_autotune_graph_replay_and_bad_code(L, mixed):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.post.cpu().numpy()[keep], ref.post.cpu().numpy()[keep])
         np.testing.assert_array_equal(out.iters.cpu().numpy(), ref.iters.cpu().numpy())
+
+
+def test_mixed_matches_the_oracle_on_every_code(L, mixed):
+    """Every one of the 15 codes of the serving mix, 6 frames each, decoded in
+    one mixed launch (FP32 messages, early stop after at most 50 iterations,
+    Eb/N0 ~ U[1, 4] dB per frame) against the FP64 oracle: the FP32 parity
+    gate per frame, with equal iteration counts on the stable frames."""
+    hs, _, codes = mixed
+    per = 6
+    fc = np.repeat(np.arange(len(hs), dtype=np.int32), per)
+    np.random.default_rng(403).shuffle(fc)
+    fc, llrs = _batch(mixed, len(fc), seed=403, fc=fc)
+    plan = L.MixedPlan(codes, msg_fp16=False)
+    b = plan.batch(fc)
+    res = plan.decode(b, torch.from_numpy(np.concatenate(llrs)).cuda(), max_iters=50, early_stop=True)
+    torch.cuda.synchronize()
+    got = _split(plan, b, res, fc)
+    excluded = 0
+    for c, h in enumerate(hs):
+        fr = np.nonzero(fc == c)[0]
+        assert fr.size == per
+        llr = np.stack([llrs[f] for f in fr])
+        post = np.stack([got[f][0] for f in fr])
+        hard = S.unpack_bits(np.stack([got[f][1] for f in fr]).view(np.uint32), h.n)
+        its = np.array([got[f][2] for f in fr])
+        ok = np.array([got[f][3] for f in fr])
+        rep = assert_fp32_parity(h, llr, 50, post, hard, its, ok, early_stop=True, max_excluded=None)
+        excluded += rep.excluded
+    assert excluded <= 0.05 * len(fc), excluded
