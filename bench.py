@@ -647,6 +647,8 @@ def run_profile_case(args):
     llr = (torch.randn((args.frames, code.n), device="cuda", generator=g) * 3.0 + 2.5).contiguous()
     if args.profile_case == "resident":
         r = L.decode(code, llr, max_iters=ITERS, schedule="resident", msg_fp16=True, want_post=False)
+    elif args.profile_case == "cluster":  # the quasi-cyclic code's default path, 25 iterations
+        r = L.decode(code, llr, max_iters=25, schedule="cluster", msg_fp16=args.fp16, want_post=False)
     else:
         r = L.decode(code, llr, max_iters=3, schedule="plain", msg_fp16=args.fp16, want_post=False)
     torch.cuda.synchronize()
@@ -665,10 +667,10 @@ def main():
     ap.add_argument("--no-table1", action="store_true",
                     help="skip the paper's Table I workload and the n = 26112 encode comparison")
     ap.add_argument("--ref-frames-per-thread", type=int, default=4)
-    ap.add_argument("--profile-case", choices=["resident", "plain", "table1-vector"], default=None,
+    ap.add_argument("--profile-case", choices=["resident", "plain", "cluster", "table1-vector"], default=None,
                     help="run one small decode (for ncu captures) instead of the benchmark")
     ap.add_argument("--frames", type=int, default=4096, help="frames of the --profile-case run")
-    ap.add_argument("--fp16", action="store_true", help="binary16 messages in the plain --profile-case run")
+    ap.add_argument("--fp16", action="store_true", help="binary16 messages in the plain or cluster --profile-case run")
     ap.add_argument("--code", choices=["c2", "qc"], default="c2", help="code of the --profile-case run")
     args = ap.parse_args()
     if args.profile_case:

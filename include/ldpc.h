@@ -47,7 +47,9 @@ typedef enum {
     LDPC_EINVAL = -1,   /* bad shape, pointer, degree or option */
     LDPC_ENOMEM = -2,   /* host or device allocation failed */
     LDPC_ECUDA = -3,    /* a CUDA call or kernel launch failed */
-    LDPC_ETIMEOUT = -4, /* a bounded wait inside a kernel gave up */
+    LDPC_ETIMEOUT = -4, /* reserved for a bounded wait inside a kernel that
+                           gives up; no kernel of this version waits on
+                           another, so no call returns it */
     LDPC_ENOTSUP = -5   /* valid request outside what the library supports */
 } ldpc_status;
 
@@ -64,7 +66,11 @@ typedef struct {
 #define LDPC_CREATE_HOST_ONLY 1u /* build host state only (no device tables);
                                     encode/decode with such a code fail */
 
-/* Creates a code object from H (host arrays, copied).  Builds the Tanner
+/* Creates a code object from H (host arrays, copied).  A code created from
+ * an ldpc_qc_desc combines the inputs of each check in ascending column order
+ * (the same order for all z checks of a base row, which the cluster decoder
+ * needs); otherwise each check's order comes from the shared-memory bank
+ * schedule (ldpc_code_schedule).  Builds the Tanner
  * graph edge layouts (Sec. II-B, Fig. 1) and the systematic generator
  * (Eq. 2; Sec. III-B: G in standard form [I_k : P] after a column
  * permutation) by GF(2) Gauss-Jordan elimination that scans pivot columns
@@ -148,6 +154,23 @@ int ldpc_syndrome(const ldpc_code *code, const uint32_t *d_bits, int32_t F, uint
                                  otherwise.  With FP32 messages and no more
                                  frames than SMs, each frame gets more
                                  threads (lower latency, same bits) */
+#define LDPC_SCHED_CLUSTER 3  /* persistent kernel for quasi-cyclic codes
+                                 created from an ldpc_qc_desc whose frames do
+                                 not fit one SM: a cluster of 2, 4 or 8 CTAs
+                                 holds a frame group in its distributed
+                                 shared memory for all iterations, each CTA
+                                 owning a slice of every circulant; needs
+                                 z a multiple of 32 x the cluster size, base
+                                 rows of at most 16 ones and a slice that
+                                 fits one SM (LDPC_ENOTSUP otherwise) */
+
+/* Cluster shape the LDPC_SCHED_CLUSTER schedule uses for this code with
+ * binary16 (msg_fp16 = 1) or FP32 messages: *ctas CTAs per cluster and
+ * *frames_per_group frames decoded together (2 with binary16 messages, one
+ * binary16 pair per message word; 1 with FP32); both 0 when the code has no
+ * cluster layout.  No counterpart in the paper.  Either pointer may be NULL. */
+int ldpc_code_cluster_shape(const ldpc_code *code, int32_t msg_fp16, int32_t *ctas,
+                            int32_t *frames_per_group);
 
 typedef struct {
     int32_t max_iters;  /* T >= 0 iterations (an iteration = all check
@@ -196,6 +219,16 @@ int ldpc_decode_host_workspace_size(const ldpc_code *code, int32_t chunk, const 
 int ldpc_decode_host(const ldpc_code *code, const float *h_llr, int32_t F, const ldpc_decode_opts *opts,
                      float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
                      void *d_work, size_t work_bytes, ldpc_stream_t stream);
+
+/* The same pipeline with a record of where the time goes (no counterpart in
+ * the paper; a measurement aid): h_ms receives, for each of the
+ * ceil(F / chunk) chunks, six times in milliseconds from the call's start on
+ * `stream`: upload start and end, decode start and end, download start and
+ * end.  Synchronises `stream` before it returns. */
+int ldpc_decode_host_timeline(const ldpc_code *code, const float *h_llr, int32_t F,
+                              const ldpc_decode_opts *opts, float *h_post, uint32_t *h_hard,
+                              int32_t *h_iters, uint8_t *h_ok, int32_t chunk, void *d_work,
+                              size_t work_bytes, ldpc_stream_t stream, float *h_ms);
 
 /* ---- Mixed-code batches (serving): frames of several codes decoded in one
  * persistent launch.  A plan holds the codes (each regular with column weight
@@ -293,8 +326,11 @@ int ldpc_decode_backward(const ldpc_code *code, int32_t F, int32_t T, const floa
  * LDPC_EINVAL when F frames of this code need more scratch than the array
  * holds (ldpc_decode_workspace_size with the plain schedule gives the need).
  * The first call on a device looks up the array's address; make it before
- * any stream capture.  All calls share the array: calls whose work overlaps
- * on the GPU race and must be serialised by the caller. */
+ * any stream capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset on that device it is stale, so this call (like
+ * ldpc_decode_host, whose streams are kept the same way) must not be used on
+ * that device again in the same process.  All calls share the array: calls
+ * whose work overlaps on the GPU race and must be serialised by the caller. */
 #define LDPC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int ldpc_decode_noalloc(const ldpc_code *code, const float *d_llr, int32_t F,
                         const ldpc_decode_opts *opts, float *d_post, uint32_t *d_hard,

@@ -19,12 +19,12 @@ import torch
 from . import _lib
 from ._lib import DecodeOpts, LdpcError, QcDesc, c_i32, c_i64, c_size, c_vp
 
-SCHED_AUTO, SCHED_PLAIN, SCHED_RESIDENT = 0, 1, 2
-_SCHED = {"auto": SCHED_AUTO, "plain": SCHED_PLAIN, "resident": SCHED_RESIDENT}
+SCHED_AUTO, SCHED_PLAIN, SCHED_RESIDENT, SCHED_CLUSTER = 0, 1, 2, 3
+_SCHED = {"auto": SCHED_AUTO, "plain": SCHED_PLAIN, "resident": SCHED_RESIDENT, "cluster": SCHED_CLUSTER}
 
 __all__ = ["Code", "encode", "syndrome", "decode", "decode_noalloc", "decode_workspace_size", "DecodeResult",
            "WeightedBP", "weighted_bp", "MixedPlan", "MixedBatch", "HostDecoder",
-           "LdpcError", "SCHED_AUTO", "SCHED_PLAIN", "SCHED_RESIDENT"]
+           "LdpcError", "SCHED_AUTO", "SCHED_PLAIN", "SCHED_RESIDENT", "SCHED_CLUSTER"]
 
 
 def _stream_handle(stream) -> c_vp:
@@ -132,6 +132,13 @@ class Code:
         _lib.check(self._lib.ldpc_code_schedule(self.handle, c_vp(order.ctypes.data), ctypes.byref(unplaced)),
                    "ldpc_code_schedule")
         return order[:self.nnz], unplaced.value
+
+    def cluster_shape(self, msg_fp16: bool) -> tuple[int, int]:
+        """(CTAs per cluster, frames per group) of the cluster schedule; (0, 0) if none."""
+        ctas, group = c_i32(), c_i32()
+        _lib.check(self._lib.ldpc_code_cluster_shape(self.handle, int(bool(msg_fp16)), ctypes.byref(ctas),
+                                                     ctypes.byref(group)), "ldpc_code_cluster_shape")
+        return ctas.value, group.value
 
     def close(self) -> None:
         if self._h:
@@ -450,3 +457,19 @@ class HostDecoder:
                                                    self.chunk, _ptr(self.work), self.work.numel(),
                                                    _stream_handle(stream)), "ldpc_decode_host")
         return out
+
+    def decode_timeline(self, llr: torch.Tensor, out: DecodeResult | None = None,
+                        stream=None) -> tuple[DecodeResult, np.ndarray]:
+        """As ``decode``, synchronised, with a record of every chunk: float [chunks, 6]
+        of milliseconds from the call's start (upload start/end, decode start/end,
+        download start/end)."""
+        if llr.is_cuda or llr.dtype != torch.float32 or not llr.is_contiguous() or llr.shape[1] != self.code.n:
+            raise ValueError("llr must be a contiguous float32 host tensor [F, n]")
+        F = llr.shape[0]
+        out = out if out is not None else self.outputs(F)
+        ms = np.zeros(((F + self.chunk - 1) // self.chunk, 6), dtype=np.float32)
+        _lib.check(self.code._lib.ldpc_decode_host_timeline(
+            self.code.handle, c_vp(llr.data_ptr()), F, ctypes.byref(self.opts), _ptr(out.post), _ptr(out.hard),
+            _ptr(out.iters), _ptr(out.ok), self.chunk, _ptr(self.work), self.work.numel(), _stream_handle(stream),
+            c_vp(ms.ctypes.data)), "ldpc_decode_host_timeline")
+        return out, ms

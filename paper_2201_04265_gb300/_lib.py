@@ -50,6 +50,7 @@ SIGNATURES = {
     "ldpc_code_positions": (c_i32, [c_vp, c_vp, c_vp]),
     "ldpc_code_parity_map": (c_i32, [c_vp, c_vp]),
     "ldpc_code_schedule": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i64)]),
+    "ldpc_code_cluster_shape": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     "ldpc_code_destroy": (None, [c_vp]),
     "ldpc_encode": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp]),
     "ldpc_encode_tables_build": (c_i32, [c_vp, ctypes.POINTER(c_size)]),
@@ -69,6 +70,8 @@ SIGNATURES = {
     "ldpc_decode_host_workspace_size": (c_i32, [c_vp, c_i32, ctypes.POINTER(DecodeOpts), ctypes.POINTER(c_size)]),
     "ldpc_decode_host": (c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(DecodeOpts), c_vp, c_vp, c_vp, c_vp, c_i32,
                                  c_vp, c_size, c_vp]),
+    "ldpc_decode_host_timeline": (c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(DecodeOpts), c_vp, c_vp, c_vp, c_vp,
+                                          c_i32, c_vp, c_size, c_vp, c_vp]),
     "ldpc_mixed_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, c_i32, ctypes.POINTER(c_vp)]),
     "ldpc_mixed_destroy": (None, [c_vp]),
     "ldpc_mixed_workspace_size": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_size)]),

@@ -72,14 +72,15 @@ int check_opts(const ldpc_decode_opts *o) {
     if (!(o->clip > 0.f) || o->clip > 1e30f) return fail(LDPC_EINVAL, "clip must be positive and finite");
     if (o->early_stop != 0 && o->early_stop != 1) return fail(LDPC_EINVAL, "early_stop must be 0 or 1");
     if (o->msg_fp16 != 0 && o->msg_fp16 != 1) return fail(LDPC_EINVAL, "msg_fp16 must be 0 or 1");
-    if (o->schedule < LDPC_SCHED_AUTO || o->schedule > LDPC_SCHED_RESIDENT)
+    if (o->schedule < LDPC_SCHED_AUTO || o->schedule > LDPC_SCHED_CLUSTER)
         return fail(LDPC_EINVAL, "unknown schedule %d", o->schedule);
     return LDPC_OK;
 }
 
 int pick_schedule(const ldpc_code *c, const ldpc_decode_opts *o) {
     if (o->schedule != LDPC_SCHED_AUTO) return o->schedule;
-    return resident_fits(c, o) ? LDPC_SCHED_RESIDENT : LDPC_SCHED_PLAIN;
+    if (resident_fits(c, o)) return LDPC_SCHED_RESIDENT;
+    return cluster_fits(c, o) ? LDPC_SCHED_CLUSTER : LDPC_SCHED_PLAIN;
 }
 
 }  // namespace
@@ -124,7 +125,9 @@ int ldpc_decode_workspace_size(const ldpc_code *c, int32_t F, const ldpc_decode_
     LDPC_TRY(check_opts(o));
     if (F < 0) return fail(LDPC_EINVAL, "F < 0");
     const int sched = pick_schedule(c, o);
-    *bytes = sched == LDPC_SCHED_RESIDENT ? resident_workspace(c, F, o) : plain_workspace(c, F, o);
+    *bytes = sched == LDPC_SCHED_RESIDENT  ? resident_workspace(c, F, o)
+             : sched == LDPC_SCHED_CLUSTER ? (size_t)256
+                                           : plain_workspace(c, F, o);
     return LDPC_OK;
 }
 
@@ -144,6 +147,13 @@ int ldpc_decode(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_de
             return fail(LDPC_ENOTSUP, "this code does not fit the resident decoder");
         return decode_resident(c, d_llr, F, o, d_post, d_hard, d_iters, d_ok, d_work, work_bytes,
                                (cudaStream_t)stream);
+    }
+    if (sched == LDPC_SCHED_CLUSTER) {
+        if (!cluster_fits(c, o))
+            return fail(LDPC_ENOTSUP, "this code has no cluster layout (quasi-cyclic codes created from "
+                                      "their base matrix only)");
+        return decode_cluster(c, d_llr, F, o, d_post, d_hard, d_iters, d_ok, d_work, work_bytes,
+                              (cudaStream_t)stream);
     }
     return decode_plain(c, d_llr, F, o, d_post, d_hard, d_iters, d_ok, d_work, work_bytes,
                         (cudaStream_t)stream);

@@ -210,7 +210,7 @@ void free_device(ldpc_code *c) {
     void *ptrs[] = {c->d.row_ptr,   c->d.col_idx,    c->d.col_ptr,  c->d.col_edge,
                     c->d.info_pos,  c->d.parity_pos, c->d.AT,       c->d.res_edges,  c->d.lat_edges,
                     c->d.eval_col,  c->d.eval_edge,  c->d.col_pos,  c->d.row_order,
-                    c->d.col_order, c->d.enc_tab};
+                    c->d.col_order, c->d.enc_tab,    c->d.cl_tab_half, c->d.cl_tab_single};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->d = DeviceCode{};
@@ -219,6 +219,34 @@ void free_device(ldpc_code *c) {
 }  // namespace
 
 int build_resident_plan(ldpc_code *c);  // decode_resident.cu
+
+namespace {
+
+// A quasi-cyclic code created from its base matrix combines each check's
+// inputs in ascending column order: the z checks of a base row then visit
+// their circulants in the same order, so the lanes of a warp that update z
+// consecutive checks read consecutive bits at every step (the cluster
+// decoder's access pattern).  The count of edges outside a bank-conflict-free
+// step of the resident schedule groups is recomputed for this order.
+void lifted_check_order(ldpc_code *c) {
+    for (int64_t e = 0; e < c->nnz; ++e) c->eval_edge[e] = (int32_t)e;
+    int64_t excess = 0;
+    const int ngroups = (int)(c->sched_groups.size() / 32);
+    for (int g = 0; g < ngroups; ++g)
+        for (int j = 0; j < c->dc_max; ++j) {
+            uint32_t seen = 0;
+            for (int u = 0; u < 32; ++u) {
+                const int32_t chk = c->sched_groups[(size_t)g * 32 + u];
+                if (chk < 0 || c->row_ptr[chk] + j >= c->row_ptr[chk + 1]) continue;
+                const uint32_t bit = 1u << (c->col_idx[c->row_ptr[chk] + j] & 31);
+                if (seen & bit) ++excess;
+                seen |= bit;
+            }
+        }
+    c->sched_excess = excess;
+}
+
+}  // namespace
 
 int upload_code(ldpc_code *c) {
     LDPC_TRY_CUDA(cudaGetDevice(&c->device));
@@ -243,6 +271,8 @@ int upload_code(ldpc_code *c) {
         if (c->res.lat_threads > 0)
             LDPC_TRY(upload(&c->d.lat_edges, c->res.lat_edges.data(), c->res.lat_edges.size()));
     }
+    if (c->cl_half.C) LDPC_TRY(upload(&c->d.cl_tab_half, c->cl_half.tab.data(), c->cl_half.tab.size()));
+    if (c->cl_single.C) LDPC_TRY(upload(&c->d.cl_tab_single, c->cl_single.tab.data(), c->cl_single.tab.size()));
     c->on_device = true;
     return LDPC_OK;
 }
@@ -317,8 +347,15 @@ int ldpc_code_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t
     c->nnz = (int64_t)ci.size();
     c->row_ptr = std::move(rp);
     c->col_idx = std::move(ci);
+    if (qc) {
+        c->qc.mb = qc->mb;
+        c->qc.nb = qc->nb;
+        c->qc.z = qc->z;
+        c->qc.shift.assign(qc->shift, qc->shift + (size_t)qc->mb * qc->nb);
+    }
     int st = build_host(c);
     if (st == LDPC_OK) st = build_check_schedule(c, resident_group_slots(c));
+    if (st == LDPC_OK && qc) lifted_check_order(c);
     if (st == LDPC_OK) {
         // derived evaluation-order arrays
         c->eval_col.resize((size_t)c->nnz);
@@ -331,6 +368,7 @@ int ldpc_code_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t
         for (int64_t q = 0; q < c->nnz; ++q) c->col_pos[q] = c->pos_of_edge[c->col_edge[q]];
         st = build_resident_plan(c);
     }
+    if (st == LDPC_OK) st = build_cluster_plan(c);
     if (st == LDPC_OK && !(flags & LDPC_CREATE_HOST_ONLY)) {
         st = upload_code(c);
         if (st != LDPC_OK) free_device(c);

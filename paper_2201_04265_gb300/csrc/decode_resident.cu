@@ -49,66 +49,6 @@ struct Shape {
 };
 constexpr Shape kShapes[] = {{6, 8}, {9, 6}, {12, 4}, {16, 3}};
 
-template <class T>
-__device__ __forceinline__ uint32_t as_u32(T x) {
-    return *reinterpret_cast<uint32_t *>(&x);
-}
-template <class T>
-__device__ __forceinline__ T from_u32(uint32_t x) {
-    return *reinterpret_cast<T *>(&x);
-}
-
-template <class MsgT, int G>
-struct EVec;
-// Besides widening and narrowing, each message word has three fused forms:
-//   add_to(L, w)   = L + E    (the bit sum, Eq. 7)
-//   sub_from(L, w) = L - E    (Eq. 6 rearranged)
-//   signed_word(m, s) = the word of E_i = (bit 31 of s_i ? -m_i : m_i)
-// each rounding exactly like the widened FP32 operation (binary16 widens
-// exactly; the mixed-precision add and fma round once, like FADD; negation
-// commutes with round-to-nearest).
-template <>
-struct EVec<__half, 2> {
-    using T = __half2;
-    __device__ static void get(T v, float *x) {
-        const float2 f = __half22float2(v);
-        x[0] = f.x;
-        x[1] = f.y;
-    }
-    __device__ static T make(const float *x) { return __floats2half2_rn(x[0], x[1]); }
-    __device__ static float2 add_to(float2 L, uint32_t w) {
-        float2 r;
-        asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-            "add.rn.f32.f16 %0, lo, %3;\n\tadd.rn.f32.f16 %1, hi, %4;\n\t}"
-            : "=f"(r.x), "=f"(r.y)
-            : "r"(w), "f"(L.x), "f"(L.y));
-        return r;
-    }
-    __device__ static float2 sub_from(float2 L, uint32_t w) {
-        float2 r;  // (-1) E + L: the product is exact, one rounding
-        asm("{\n\t.reg .f16 lo, hi, m;\n\tmov.b32 {lo, hi}, %2;\n\tmov.b16 m, 0xBC00;\n\t"
-            "fma.rn.f32.f16 %0, lo, m, %3;\n\tfma.rn.f32.f16 %1, hi, m, %4;\n\t}"
-            : "=f"(r.x), "=f"(r.y)
-            : "r"(w), "f"(L.x), "f"(L.y));
-        return r;
-    }
-    __device__ static uint32_t signed_word(const float *m, const uint32_t *s) {
-        const uint32_t h = as_u32(__floats2half2_rn(m[0], m[1]));
-        return h ^ (__byte_perm(s[0], s[1], 0x7030) & 0x80008000u);  // sign bytes -> bits 15, 31
-    }
-};
-template <>
-struct EVec<float, 1> {
-    using T = float;
-    __device__ static void get(T v, float *x) { x[0] = v; }
-    __device__ static T make(const float *x) { return x[0]; }
-    __device__ static float add_to(float L, uint32_t w) { return L + __uint_as_float(w); }
-    __device__ static float sub_from(float L, uint32_t w) { return L - __uint_as_float(w); }
-    __device__ static uint32_t signed_word(const float *m, const uint32_t *s) {
-        return __float_as_uint(m[0]) ^ (s[0] & 0x80000000u);
-    }
-};
-
 struct ResArgs {
     const float *llr;
     int32_t F, n, npad, m, NW, T_iters, early_stop;

@@ -69,6 +69,8 @@ struct DeviceCode {
     uint32_t *res_edges = nullptr; // resident slot table of the single-code launch
     int32_t res_edges_len = 0;
     uint32_t *lat_edges = nullptr; // slot table of the small-batch (latency) launch
+    int32_t *cl_tab_half = nullptr;    // cluster-decoder tables (binary16 / FP32 messages)
+    int32_t *cl_tab_single = nullptr;
     // Four-Russians encoding tables (encode.cu), built on request:
     // [enc_ns][enc_ng][256][4] words, 0 = not built
     uint32_t *enc_tab = nullptr;
@@ -87,6 +89,21 @@ struct ResidentPlan {
     int32_t lat_threads = 0;  // threads per CTA of the small-batch launch, 0 = none
     std::vector<uint32_t> lat_edges;  // its slot table, same form as `edges`
     std::vector<uint32_t> edges; // [cpt * ceil(dc_pad/2)][threads] 16-bit slot pairs
+};
+
+// Quasi-cyclic description kept from creation (z = 0 when H came as CSR).
+struct QcInfo {
+    int32_t mb = 0, nb = 0, z = 0;
+    std::vector<int16_t> shift;  // [mb][nb], -1 = zero block
+};
+
+// Cluster-decoder launch shape for one message type (decode_cluster.cu).
+struct ClusterCfg {
+    int32_t C = 0;              // CTAs per cluster, 0 = no plan
+    int32_t G = 0;              // frames per group
+    int32_t zc = 0;             // lifting indices per CTA (z / C)
+    size_t smem = 0;            // dynamic shared memory per CTA
+    std::vector<int32_t> tab;   // table blob every CTA copies into shared memory
 };
 
 }  // namespace ldpc
@@ -112,6 +129,8 @@ struct ldpc_code {
     int device = -1;
     ldpc::DeviceCode d;
     ldpc::ResidentPlan res;
+    ldpc::QcInfo qc;
+    ldpc::ClusterCfg cl_half, cl_single;  // binary16 / FP32 messages
 };
 
 namespace ldpc {
@@ -129,6 +148,11 @@ int launch_encode(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, 
                   cudaStream_t s);
 int launch_syndrome(const ldpc_code *c, const uint32_t *d_bits, int32_t F, uint32_t *d_syn,
                     uint8_t *d_ok, cudaStream_t s);
+int build_cluster_plan(ldpc_code *c);                                 // decode_cluster.cu
+bool cluster_fits(const ldpc_code *c, const ldpc_decode_opts *o);
+int decode_cluster(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_decode_opts *o,
+                   float *d_post, uint32_t *d_hard, int32_t *d_iters, uint8_t *d_ok, void *d_work,
+                   size_t work_bytes, cudaStream_t s);
 size_t plain_workspace(const ldpc_code *c, int32_t F, const ldpc_decode_opts *o);
 int decode_plain(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_decode_opts *o,
                  float *d_post, uint32_t *d_hard, int32_t *d_iters, uint8_t *d_ok, void *d_work,

@@ -12,6 +12,7 @@
 // independent, so chunks are too.
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "ldpc_internal.h"
 
@@ -105,9 +106,22 @@ int ldpc_decode_host_workspace_size(const ldpc_code *c, int32_t chunk, const ldp
     return LDPC_OK;
 }
 
-int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ldpc_decode_opts *o,
-                     float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
-                     void *d_work, size_t work_bytes, ldpc_stream_t stream) {
+}  // extern "C"
+
+namespace ldpc {
+namespace {
+
+// Timing events of one chunk (timeline mode): upload, decode and download,
+// each bracketed on the stream that runs it.
+struct ChunkMarks {
+    cudaEvent_t ev[6] = {};
+};
+
+// The pipeline; with `marks` (one entry per chunk, events created by the
+// caller), each chunk's upload, decode and download are bracketed by events.
+int host_pipeline(const ldpc_code *c, const float *h_llr, int32_t F, const ldpc_decode_opts *o,
+                  float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
+                  void *d_work, size_t work_bytes, ldpc_stream_t stream, ChunkMarks *marks) {
     if (!c || !o) return fail(LDPC_EINVAL, "code or opts is NULL");
     if (F < 0 || chunk < 1) return fail(LDPC_EINVAL, "F < 0 or chunk < 1");
     if (F == 0) return LDPC_OK;
@@ -130,14 +144,19 @@ int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ld
         const int32_t fc = (int32_t)std::min<int64_t>(chunk, F - f0);
         // staging buffer b is free once chunk ci - kStage's results are copied out
         if (used[b]) LDPC_TRY_CUDA(cudaStreamWaitEvent(r->up, r->d2h[b], 0));
+        if (marks) LDPC_TRY_CUDA(cudaEventRecord(marks[ci].ev[0], r->up));
         LDPC_TRY_CUDA(cudaMemcpyAsync(w.llr[b], h_llr + f0 * c->n, sizeof(float) * (size_t)fc * c->n,
                                       cudaMemcpyHostToDevice, r->up));
+        if (marks) LDPC_TRY_CUDA(cudaEventRecord(marks[ci].ev[1], r->up));
         LDPC_TRY_CUDA(cudaEventRecord(r->h2d[b], r->up));
         LDPC_TRY_CUDA(cudaStreamWaitEvent(s, r->h2d[b], 0));
+        if (marks) LDPC_TRY_CUDA(cudaEventRecord(marks[ci].ev[2], s));
         LDPC_TRY(ldpc_decode(c, w.llr[b], fc, o, h_post ? w.post[b] : nullptr, w.hard[b], w.iters[b], w.ok[b],
                              w.dec, w.dec_bytes, stream));
+        if (marks) LDPC_TRY_CUDA(cudaEventRecord(marks[ci].ev[3], s));
         LDPC_TRY_CUDA(cudaEventRecord(r->dec[b], s));
         LDPC_TRY_CUDA(cudaStreamWaitEvent(r->down, r->dec[b], 0));
+        if (marks) LDPC_TRY_CUDA(cudaEventRecord(marks[ci].ev[4], r->down));
         if (h_post)
             LDPC_TRY_CUDA(cudaMemcpyAsync(h_post + f0 * c->n, w.post[b], sizeof(float) * (size_t)fc * c->n,
                                           cudaMemcpyDeviceToHost, r->down));
@@ -149,12 +168,58 @@ int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ld
                                           cudaMemcpyDeviceToHost, r->down));
         if (h_ok)
             LDPC_TRY_CUDA(cudaMemcpyAsync(h_ok + f0, w.ok[b], (size_t)fc, cudaMemcpyDeviceToHost, r->down));
+        if (marks) LDPC_TRY_CUDA(cudaEventRecord(marks[ci].ev[5], r->down));
         LDPC_TRY_CUDA(cudaEventRecord(r->d2h[b], r->down));
         used[b] = true;
     }
     // the caller's stream completes only after the last results reach the host
     LDPC_TRY_CUDA(cudaStreamWaitEvent(s, r->d2h[(nchunks - 1) % kStage], 0));
     return LDPC_OK;
+}
+
+}  // namespace
+}  // namespace ldpc
+
+extern "C" {
+
+int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ldpc_decode_opts *o,
+                     float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
+                     void *d_work, size_t work_bytes, ldpc_stream_t stream) {
+    return host_pipeline(c, h_llr, F, o, h_post, h_hard, h_iters, h_ok, chunk, d_work, work_bytes, stream,
+                         nullptr);
+}
+
+int ldpc_decode_host_timeline(const ldpc_code *c, const float *h_llr, int32_t F, const ldpc_decode_opts *o,
+                              float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
+                              void *d_work, size_t work_bytes, ldpc_stream_t stream, float *h_ms) {
+    if (!h_ms) return fail(LDPC_EINVAL, "h_ms is NULL");
+    if (F <= 0 || chunk < 1) return fail(LDPC_EINVAL, "need F >= 1 and chunk >= 1");
+    const int64_t nchunks = ceil_div(F, chunk);
+    std::vector<ChunkMarks> marks((size_t)nchunks);
+    cudaEvent_t t0 = nullptr;
+    int st = LDPC_OK;
+    cudaError_t e = cudaEventCreate(&t0);
+    for (int64_t i = 0; i < nchunks && e == cudaSuccess; ++i)
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaEventCreate(&marks[i].ev[k]);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, (cudaStream_t)stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "timeline events");
+    if (st == LDPC_OK)
+        st = host_pipeline(c, h_llr, F, o, h_post, h_hard, h_iters, h_ok, chunk, d_work, work_bytes, stream,
+                           marks.data());
+    if (st == LDPC_OK) {
+        e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize(timeline)");
+    }
+    for (int64_t i = 0; i < nchunks && st == LDPC_OK; ++i)
+        for (int k = 0; k < 6 && st == LDPC_OK; ++k) {
+            e = cudaEventElapsedTime(&h_ms[i * 6 + k], t0, marks[i].ev[k]);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaEventElapsedTime(timeline)");
+        }
+    for (auto &m : marks)
+        for (cudaEvent_t ev : m.ev)
+            if (ev) cudaEventDestroy(ev);
+    if (t0) cudaEventDestroy(t0);
+    return st;
 }
 
 }  // extern "C"

@@ -17,7 +17,7 @@ import torch
 
 import ldpc_synth as S
 import oracle
-from parity_util import fp32_conditioned_frames, hard_close, llr_close
+from parity_util import CLIP, assert_fp32_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +56,7 @@ def c2(L):
     for f0 in range(0, F2, 8192):
         fr = np.arange(f0, f0 + 8192)
         llr[f0:f0 + 8192] = S.bpsk_awgn_llr(cw[fr], EBN0_2, rate, S.frame_noise(F2, h.n, SEED2 + 1, frames=fr))
-    sample = np.random.default_rng(5).choice(F2, 12, replace=False)
+    sample = np.random.default_rng(5).choice(F2, 40, replace=False)
     return h, sysm, code, cw, torch.from_numpy(llr).cuda(), sample, rate
 
 
@@ -94,26 +94,47 @@ def test_c2_encode_full_batch_tables(L, c2):
 
 @pytest.mark.parametrize("fp16", [False, True])
 def test_c2_decode_full_batch_sampled_frames(L, c2, fp16):
+    """The whole 65536-frame batch on the resident decoder in the benchmark's
+    configuration; 40 sampled frames against the FP64 oracle.  FP32 messages:
+    the FP32 parity gate.  Binary16 messages (parity unpinned at 1e-3 by
+    design): hard decisions of every frame the oracle decodes agree, and the
+    clipped LLR error against FP64 is bounded by what binary16 rounding of
+    messages of up to 20 can add over 50 iterations."""
     h, sysm, code, cw, llr, sample, rate = c2
     res = L.decode(code, llr, max_iters=T2, schedule="resident", msg_fp16=fp16)
     torch.cuda.synchronize()
     post = res.post.cpu().numpy()[sample]
     hard = S.unpack_bits(res.hard.cpu().numpy()[sample].view(np.uint32), h.n)
     ok = res.ok.cpu().numpy()[sample]
+    iters = res.iters.cpu().numpy()[sample]
     _, ollr = _oracle_frames(h, sysm, rate, sample)
     np.testing.assert_array_equal(ollr, llr.cpu().numpy()[sample])   # identical inputs
-    ref = oracle.decode(h, ollr, iters=T2)
     if not fp16:
-        stable, _ = fp32_conditioned_frames(h, ollr, T2)
-        assert stable.sum() >= 10
-        assert llr_close(post[stable], ref.post[stable]).all()
-        assert hard_close(hard[stable], ref.hard[stable], ref.post[stable]).all()
-        np.testing.assert_array_equal(ok[stable], ref.ok[stable])
+        assert_fp32_parity(h, ollr, T2, post, hard, iters, ok, max_excluded=0.05)
     else:
-        # binary16 storage: hard decisions of frames the oracle decodes agree
+        ref = oracle.decode(h, ollr, iters=T2, nthreads=16)
         good = ref.ok.astype(bool)
         np.testing.assert_array_equal(hard[good], ref.hard[good])
+        err = np.abs(np.clip(post, -CLIP, CLIP) - np.clip(ref.post, -CLIP, CLIP))
+        print(f"binary16 messages, C2 at {EBN0_2} dB: max |dL| {err.max():.4g}, mean {err.mean():.4g}")
+        assert err.mean() < 0.05 and err.max() <= 2 * CLIP
     assert (res.iters.cpu().numpy() == T2).all()
+
+
+def test_c2_fp16_resident_and_fp32_plain_equal_frame_errors(L, c2):
+    """The headline comparison's gate on the full batch: the binary16 resident
+    decoder and the plain FP32 decoder fail on the same number of frames to
+    within 0.1 % of the batch, and disagree in their hard decisions on at most
+    0.1 % of the frames."""
+    h, sysm, code, cw, llr, sample, rate = c2
+    a = L.decode(code, llr, max_iters=T2, schedule="resident", msg_fp16=True, want_post=False)
+    b = L.decode(code, llr, max_iters=T2, schedule="plain", msg_fp16=False, want_post=False)
+    torch.cuda.synchronize()
+    fail16 = int((a.ok == 0).sum())
+    fail32 = int((b.ok == 0).sum())
+    differ = int((a.hard != b.hard).any(dim=1).sum())
+    assert abs(fail16 - fail32) <= 0.001 * F2, (fail16, fail32)
+    assert differ <= 0.001 * F2, differ
 
 
 @pytest.fixture(scope="module")
@@ -158,7 +179,36 @@ def test_qc_encode_full_batch_tables(L, qc):
     assert not oracle.syndrome(h, bits).any()
 
 
-def test_qc_decode_full_batch_sampled_frames(L, qc):
+@pytest.fixture(scope="module")
+def qc_sys(qc):
+    h, _ = qc
+    return oracle.systematic(h)   # about a minute: GF(2) elimination of the 17664 x 26112 H
+
+
+@pytest.mark.parametrize("ebn0", [1.0, 2.0])
+def test_qc_decode_random_codewords_against_oracle(L, qc, qc_sys, ebn0):
+    """32 random codewords of the n = 26112 quasi-cyclic code, encoded by the
+    oracle, 25 iterations with FP32 messages through the schedule this code
+    takes by default, against the FP64 oracle (FP32 parity gate).  At 1.0 dB
+    no frame decodes; at 2.0 dB all do."""
+    h, code = qc
+    F, T = 32, 25
+    msgs = S.info_bits(F, qc_sys.k, 9000)
+    cw = oracle.encode(qc_sys, msgs)
+    llr = S.bpsk_awgn_llr(cw, ebn0, qc_sys.k / h.n, S.frame_noise(F, h.n, 9001))
+    res = L.decode(code, torch.from_numpy(llr).cuda(), max_iters=T, msg_fp16=False)
+    torch.cuda.synchronize()
+    hard = S.unpack_bits(res.hard.cpu().numpy().view(np.uint32), h.n)
+    assert_fp32_parity(h, llr, T, res.post.cpu().numpy(), hard, res.iters.cpu().numpy(),
+                       res.ok.cpu().numpy(), max_excluded=0.05)
+
+
+@pytest.mark.parametrize("ebn0", [1.85, 2.0])
+def test_qc_decode_full_batch_fp16_frame_errors(L, qc, ebn0):
+    """The full 4096-frame, 25-iteration batch on the all-zero codeword (valid
+    for every linear code, so no input depends on the CUDA path): binary16
+    message storage fails on the same number of frames as FP32 messages, to
+    within 0.1 % of the batch."""
     h, code = qc
     F, T = 4096, 25
     rate = code.k / code.n
@@ -166,22 +216,13 @@ def test_qc_decode_full_batch_sampled_frames(L, qc):
     llr = np.empty((F, code.n), dtype=np.float32)
     for f0 in range(0, F, 1024):
         fr = np.arange(f0, f0 + 1024)
-        llr[f0:f0 + 1024] = S.bpsk_awgn_llr(np.broadcast_to(zero, (1024, code.n)), 1.85, rate,
+        llr[f0:f0 + 1024] = S.bpsk_awgn_llr(np.broadcast_to(zero, (1024, code.n)), ebn0, rate,
                                             S.frame_noise(F, code.n, 7400, frames=fr))
     d_llr = torch.from_numpy(llr).cuda()
-    r32 = L.decode(code, d_llr, max_iters=T, schedule="plain", msg_fp16=False)
-    r16 = L.decode(code, d_llr, max_iters=T, schedule="plain", msg_fp16=True)
+    r32 = L.decode(code, d_llr, max_iters=T, msg_fp16=False, want_post=False)
+    r16 = L.decode(code, d_llr, max_iters=T, msg_fp16=True, want_post=False)
     torch.cuda.synchronize()
-    sample = np.random.default_rng(6).choice(F, 6, replace=False)
-    stable, ref = fp32_conditioned_frames(h, llr[sample], T)
-    assert stable.sum() >= 2
-    post = r32.post.cpu().numpy()[sample][stable]
-    hard32 = _unpack(r32.hard.cpu().numpy().view(np.uint32), code.n)
-    hard16 = _unpack(r16.hard.cpu().numpy().view(np.uint32), code.n)
-    assert llr_close(post, ref.post[stable]).all()
-    assert hard_close(hard32[sample][stable], ref.hard[stable], ref.post[stable]).all()
-    # frame errors against the all-zero codeword: binary16 storage may move
-    # only frames near the decoding threshold
-    fe32 = int(hard32.any(axis=1).sum())
-    fe16 = int(hard16.any(axis=1).sum())
-    assert abs(fe32 - fe16) <= 3 + 3 * np.sqrt(fe32), (fe32, fe16)
+    fe32 = int((r32.hard != 0).any(dim=1).sum())
+    fe16 = int((r16.hard != 0).any(dim=1).sum())
+    assert 0 < fe32 < F or ebn0 == 2.0
+    assert abs(fe32 - fe16) <= 0.001 * F, (fe32, fe16)
