@@ -159,18 +159,21 @@ int ldpc_syndrome(const ldpc_code *code, const uint32_t *d_bits, int32_t F, uint
                                  not fit one SM: a cluster of 2, 4 or 8 CTAs
                                  holds a frame group in its distributed
                                  shared memory for all iterations, each CTA
-                                 owning a slice of every circulant; needs
-                                 z a multiple of 32 x the cluster size, base
-                                 rows of at most 16 ones and a slice that
-                                 fits one SM (LDPC_ENOTSUP otherwise) */
+                                 owning whole base rows and columns; needs
+                                 z a multiple of 32, base rows of at most 16
+                                 ones and a part that fits one SM
+                                 (LDPC_ENOTSUP otherwise) */
 
 /* Cluster shape the LDPC_SCHED_CLUSTER schedule uses for this code with
- * binary16 (msg_fp16 = 1) or FP32 messages: *ctas CTAs per cluster and
+ * binary16 (msg_fp16 = 1) or FP32 messages: *ctas CTAs per cluster,
  * *frames_per_group frames decoded together (2 with binary16 messages, one
- * binary16 pair per message word; 1 with FP32); both 0 when the code has no
- * cluster layout.  No counterpart in the paper.  Either pointer may be NULL. */
+ * binary16 pair per message word; 1 with FP32), and *local_fraction, the
+ * share of base-matrix entries whose row and column the partition gives to
+ * the same CTA (the rest are read from a peer CTA every iteration); all 0
+ * when the code has no cluster layout.  No counterpart in the paper.  Any
+ * pointer may be NULL. */
 int ldpc_code_cluster_shape(const ldpc_code *code, int32_t msg_fp16, int32_t *ctas,
-                            int32_t *frames_per_group);
+                            int32_t *frames_per_group, float *local_fraction);
 
 typedef struct {
     int32_t max_iters;  /* T >= 0 iterations (an iteration = all check

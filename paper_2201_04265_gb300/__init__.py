@@ -135,10 +135,15 @@ class Code:
 
     def cluster_shape(self, msg_fp16: bool) -> tuple[int, int]:
         """(CTAs per cluster, frames per group) of the cluster schedule; (0, 0) if none."""
-        ctas, group = c_i32(), c_i32()
+        return self.cluster_layout(msg_fp16)[:2]
+
+    def cluster_layout(self, msg_fp16: bool) -> tuple[int, int, float]:
+        """(CTAs per cluster, frames per group, share of base entries kept inside one CTA)."""
+        ctas, group, local = c_i32(), c_i32(), ctypes.c_float()
         _lib.check(self._lib.ldpc_code_cluster_shape(self.handle, int(bool(msg_fp16)), ctypes.byref(ctas),
-                                                     ctypes.byref(group)), "ldpc_code_cluster_shape")
-        return ctas.value, group.value
+                                                     ctypes.byref(group), ctypes.byref(local)),
+                   "ldpc_code_cluster_shape")
+        return ctas.value, group.value, float(local.value)
 
     def close(self) -> None:
         if self._h:

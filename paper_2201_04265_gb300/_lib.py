@@ -50,7 +50,8 @@ SIGNATURES = {
     "ldpc_code_positions": (c_i32, [c_vp, c_vp, c_vp]),
     "ldpc_code_parity_map": (c_i32, [c_vp, c_vp]),
     "ldpc_code_schedule": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i64)]),
-    "ldpc_code_cluster_shape": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "ldpc_code_cluster_shape": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
+                                        ctypes.POINTER(ctypes.c_float)]),
     "ldpc_code_destroy": (None, [c_vp]),
     "ldpc_encode": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_vp]),
     "ldpc_encode_tables_build": (c_i32, [c_vp, ctypes.POINTER(c_size)]),

@@ -101,7 +101,11 @@ struct QcInfo {
 struct ClusterCfg {
     int32_t C = 0;              // CTAs per cluster, 0 = no plan
     int32_t G = 0;              // frames per group
-    int32_t zc = 0;             // lifting indices per CTA (z / C)
+    uint32_t e_bytes = 0;       // message planes per CTA
+    uint32_t l_bytes = 0;       // total planes per CTA
+    int32_t internal = 0;       // base entries whose row and column share a CTA
+    int32_t entries = 0;        // base entries
+    int32_t sec_words = 0;      // words of the largest per-CTA table section
     size_t smem = 0;            // dynamic shared memory per CTA
     std::vector<int32_t> tab;   // table blob every CTA copies into shared memory
 };

@@ -17,14 +17,16 @@ from parity_util import assert_fp32_parity
 
 pytestmark = pytest.mark.gpu
 
-# (mb, nb, nonzeros, row weight min, max, z, seed): cluster of 2 (z = 64),
-# 4 (the 46 x 68, z = 384 workload code) and 8 CTAs (the same base, z = 768)
+# (mb, nb, nonzeros, row weight min, max, z, seed): clusters of 2 CTAs
+# (z = 64), 4 (the 46 x 68, z = 384 workload code) and, with binary16
+# messages, 8 (a 24 x 48 base lifted by 768)
 QC = {
     "z64": (8, 16, 40, 3, 8, 64, 2),
     "c3_z384": (46, 68, 316, 3, 19, 384, 3),
-    "z768": (46, 68, 316, 3, 19, 768, 3),
+    "z768": (24, 48, 200, 3, 14, 768, 4),
 }
-CTAS = {"z64": 2, "c3_z384": 4, "z768": 8}
+CTAS = {("z64", True): 2, ("z64", False): 2, ("c3_z384", True): 4, ("c3_z384", False): 4,
+        ("z768", True): 8, ("z768", False): 4}
 
 
 @pytest.fixture(scope="module")
@@ -63,7 +65,9 @@ def _run(L, code, llr, **kw):
 @pytest.mark.parametrize("early_stop", [False, True])
 def test_cluster_matches_plain_bit_for_bit(L, name, fp16, early_stop):
     h, code = qc_code(L, name)
-    assert code.cluster_shape(fp16) == (CTAS[name], 2 if fp16 else 1)
+    ctas, group, local = code.cluster_layout(fp16)
+    assert (ctas, group) == (CTAS[name, fp16], 2 if fp16 else 1)
+    assert 0.4 < local <= 1.0   # share of base entries whose row and column share a CTA
     F = 9 if name == "z768" else 37   # odd: the last binary16 group holds one frame
     llr = torch.from_numpy(zero_word_llr(code.n, code.k / code.n, F, 2.0, seed=810)).cuda()
     kw = dict(max_iters=25, early_stop=early_stop, msg_fp16=fp16)
