@@ -329,6 +329,18 @@ def run_ours(args):
             e_ms = float(te.item())
         enc_ms = [m[0].elapsed_time(m[1]) for m in marks]
         hdec_ms = [m[1].elapsed_time(m[2]) for m in marks]
+        # one more pass with a record of every chunk (outside the timed steps):
+        # where the time goes between the host link and the decoder
+        _, tl = hdec.decode_timeline(host_llr[0], out=hout)
+        timeline = {"chunks": int(tl.shape[0]), "chunk_frames": 8192,
+                    "upload_ms": [round(float(x), 2) for x in tl[:, 1] - tl[:, 0]],
+                    "decode_ms": [round(float(x), 2) for x in tl[:, 3] - tl[:, 2]],
+                    "download_ms": [round(float(x), 2) for x in tl[:, 5] - tl[:, 4]],
+                    "decoder_idle_ms": [round(float(tl[i, 2] - (tl[i - 1, 3] if i else 0.0)), 2)
+                                        for i in range(tl.shape[0])],
+                    "total_ms": round(float(tl[-1, 5]), 2),
+                    "upload_gbs": round(float(host_llr[0][:8192].numel() * 4 / (np.median(tl[:, 1] - tl[:, 0]) * 1e-3)
+                                              / 1e9), 1)}
         h2d = host_llr[0].numel() * 4 + host_info.numel() * 4
         d2h = host_cw.numel() * 4 + hout.hard.numel() * 4 + hout.iters.numel() * 4 + hout.ok.numel()
         e2e = {"value": round(world * bits_per_step / (e_ms * 1e-3) / 1e9, 4), "unit": "Gbit/s",
@@ -337,7 +349,8 @@ def run_ours(args):
                "api": "encode + HostDecoder.decode (ldpc_decode_host, 8192-frame chunks)",
                "median_ms_per_step": round(statistics.median([x + y for x, y in zip(enc_ms, hdec_ms)]), 3),
                "encode_with_copies_ms": [round(x, 2) for x in enc_ms],
-               "host_decode_ms": [round(x, 2) for x in hdec_ms], "clocks": e2e_clocks.summary()}
+               "host_decode_ms": [round(x, 2) for x in hdec_ms], "clocks": e2e_clocks.summary(),
+               "timeline": timeline}
 
     # --- roofline of the dominant kernel (the resident decoder): MUFU-bound
     dec_avg_s = statistics.mean(dec_ms) * 1e-3
@@ -365,7 +378,7 @@ def run_ours(args):
     ocheck = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, sample = cpu_baseline(h, seconds=args.cpu_seconds)
-        ocheck = oracle_check(L, torch, code, sample, dev)
+        ocheck = oracle_check(L, torch, code, sample, dev, h=h)
 
     # --- the same batches with syndrome early termination (up to 50 iterations)
     early = {}
@@ -382,6 +395,10 @@ def run_ours(args):
                               "gbps": round(bits_per_step / (t_es * 1e-3) / 1e9, 4),
                               "mean_iterations": round(float(res.iters.float().mean()), 3),
                               "fer": _frame_errors(torch, res.hard, cw_words) / FRAMES}
+    extra = rank == 0 and not args.no_extra
+    c3 = bench_c3(L, torch, dev, peaks) if extra else None
+    c4 = bench_c4(L, torch, dev, peak_mufu) if extra else None
+    c5 = bench_c5(L, torch, dev, peaks) if extra else None
     table1 = paper_table1(L, torch, dev) if rank == 0 and not args.no_table1 else None
     enc_c3 = encode_c3(L, torch, dev) if rank == 0 and not args.no_table1 else None
 
@@ -410,6 +427,9 @@ def run_ours(args):
             "oracle_check": ocheck,
             "early_stop": early,
             "paper_table1": table1,
+            "c3": c3,
+            "c4": c4,
+            "c5": c5,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -473,30 +493,281 @@ def cpu_baseline(h, seconds: float = 15.0, ebn0: float = 2.0):
     return line, (llr, cw, ref)
 
 
-def oracle_check(L, torch, code, sample, dev):
+def oracle_check(L, torch, code, sample, dev, h=None):
     """The decoders on the CPU baseline's own sample (inputs made on the host by
     the oracle's encoder, none from the CUDA path), against the oracle's FP64
-    results: frame errors, hard-decision agreement, and for FP32 messages the
-    share of posteriors within 1e-4 relative / 1e-3 absolute (both clipped at
-    |L| = 20)."""
+    results: frame errors, hard-decision agreement, the clipped LLR error
+    (max and mean |dL|), and for FP32 messages the share of posteriors within
+    1e-4 relative / 1e-3 absolute (both clipped at |L| = 20).  With ``h``, the
+    same on 64 frames at 1.5 dB, where frames fail and binary16 storage shows
+    its error (at 2 dB every frame converges and saturates)."""
+    import ldpc_synth as S
+    import oracle
+
+    def one(llr, cw, ref):
+        d = torch.from_numpy(llr).to(dev)
+        res = {"frames": int(llr.shape[0]), "oracle_fer": float((ref.hard != cw).any(axis=1).mean())}
+        shifts = np.arange(32, dtype=np.uint32)
+        for name, kw in (("fp16_resident", dict(msg_fp16=True, schedule="resident")),
+                         ("fp32_plain", dict(msg_fp16=False, schedule="plain"))):
+            r = L.decode(code, d, max_iters=ITERS, early_stop=False, **kw)
+            torch.cuda.synchronize()
+            words = r.hard.cpu().numpy().view(np.uint32)
+            hard = ((words[:, :, None] >> shifts) & 1).reshape(words.shape[0], -1)[:, :code.n].astype(np.uint8)
+            post = r.post.cpu().numpy().astype(np.float64)
+            g, o = np.clip(post, -20, 20), np.clip(ref.post, -20, 20)
+            close = np.abs(g - o) <= np.maximum(1e-3, 1e-4 * np.abs(o))
+            mx, mean = _llr_err(post, ref.post)
+            res[name] = {"fer": float((hard != cw).any(axis=1).mean()),
+                         "hard_equal_oracle": float((hard == ref.hard).mean()),
+                         "post_within_tolerance": float(close.mean()),
+                         "max_abs_dL": round(mx, 5), "mean_abs_dL": round(mean, 6)}
+        return res
+
     llr, cw, ref = sample
-    d = torch.from_numpy(llr).to(dev)
-    out = {"frames": int(llr.shape[0])}
-    shifts = np.arange(32, dtype=np.uint32)
-    for name, kw in (("fp16_resident", dict(msg_fp16=True, schedule="resident")),
-                     ("fp32_plain", dict(msg_fp16=False, schedule="plain"))):
-        r = L.decode(code, d, max_iters=ITERS, early_stop=False, **kw)
-        torch.cuda.synchronize()
-        words = r.hard.cpu().numpy().view(np.uint32)
-        hard = ((words[:, :, None] >> shifts) & 1).reshape(words.shape[0], -1)[:, :code.n].astype(np.uint8)
-        post = r.post.cpu().numpy().astype(np.float64)
-        g, o = np.clip(post, -20, 20), np.clip(ref.post, -20, 20)
-        close = np.abs(g - o) <= np.maximum(1e-3, 1e-4 * np.abs(o))
-        out[name] = {"fer": float((hard != cw).any(axis=1).mean()),
-                     "hard_equal_oracle": float((hard == ref.hard).mean()),
-                     "post_within_tolerance": float(close.mean())}
-    out["oracle_fer"] = float((ref.hard != cw).any(axis=1).mean())
+    out = one(llr, cw, ref)
+    out["ebn0_db"] = 2.0
+    if h is not None:
+        sysm = oracle.systematic(h)
+        msgs = S.info_bits(64, sysm.k, 15)
+        cw15 = oracle.encode(sysm, msgs)
+        llr15 = S.bpsk_awgn_llr(cw15, 1.5, sysm.k / h.n, S.frame_noise(64, h.n, 16))
+        ref15 = oracle.decode(h, llr15, iters=ITERS, nthreads=os.cpu_count() or 1)
+        out["at_1.5dB"] = one(llr15, cw15, ref15)
     return out
+
+def _timed_ms(torch, fn, reps=5):
+    """Median CUDA-event time of fn() on the current stream, after one warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def _llr_err(post, ref_post):
+    """Max and mean |dL| of decoded LLRs against the FP64 oracle, both clipped at |L| = 20."""
+    g = np.clip(np.asarray(post, dtype=np.float64), -20, 20)
+    o = np.clip(ref_post, -20, 20)
+    d = np.abs(g - o)
+    return float(d.max()), float(d.mean())
+
+
+def bench_c3(L, torch, dev, peaks):
+    """The quasi-cyclic workload: 46 x 68 base matrix, 316 nonzeros, Z = 384
+    (n = 26112), 4096 frames, Eb/N0 1.0 .. 3.0 dB, 25 fixed iterations, on the
+    cluster-resident decoder (the default schedule for this code) with
+    binary16 and FP32 messages; the plain decoder (messages in HBM) at 2.0 dB
+    for comparison.  Inputs: the all-zero codeword (a codeword of every
+    linear code) through BPSK/AWGN, made on the device from a seeded
+    generator.  Oracle check: 8 frames per Eb/N0 from host noise, decoded on
+    the GPU through the same path and by the FP64 oracle."""
+    import ldpc_synth as S
+    import oracle
+    base = S.qc_base_matrix(46, 68, 316, 3, 19, 384, seed=3)
+    h = S.qc_expand(base, 384)
+    code = L.Code.from_qc(base, 384)
+    n, E, k = code.n, code.nnz, code.k
+    rate = k / n
+    F, T = 4096, 25
+    g = torch.Generator(device=dev)
+    g.manual_seed(3003)
+    out = {"workload": f"QC 46x68 base, 316 nonzeros, Z=384 (n={n}, k={k}, edges={E}), {F} frames, "
+                       f"{T} fixed iterations, all-zero codeword",
+           "decoder": "cluster-resident (default schedule for this code)", "points": {}}
+    for fp16 in (True, False):
+        ctas, group, local = code.cluster_layout(fp16)
+        out["cluster_fp16" if fp16 else "cluster_fp32"] = {
+            "ctas": ctas, "frames_per_group": group, "local_entry_fraction": round(local, 4)}
+    hbm = peaks.get("hbm_gbs")
+    for eb in (1.0, 1.5, 2.0, 2.5, 3.0):
+        s2 = 1.0 / (2 * rate * 10 ** (eb / 10))
+        llr = (2.0 * (-1.0 + s2 ** 0.5 * torch.randn((F, n), device=dev, generator=g)) / s2).float().contiguous()
+        pt = {}
+        for fp16 in (True, False):
+            kw = dict(max_iters=T, early_stop=False, msg_fp16=fp16, want_post=False)
+            r = L.decode(code, llr, **kw)
+            ms = _timed_ms(torch, lambda: L.decode(code, llr, out=r, **kw), reps=3)
+            fe = int((r.hard != 0).any(dim=1).sum())
+            # the HBM-equivalent bound: the bytes the plain schedule must move
+            # per frame and iteration (check: L via cache + E read/write; bit:
+            # E, R, L write), 6E + 12n with binary16, 12E + 12n with FP32
+            hbm_bytes = F * T * ((6 if fp16 else 12) * E + 12 * n)
+            gbs = hbm_bytes / (ms * 1e-3) / 1e9
+            pt["fp16" if fp16 else "fp32"] = {
+                "ms": round(ms, 3), "gbps": round(F * k / (ms * 1e-3) / 1e9, 4), "fer": fe / F,
+                "roofline": {"bound": "hbm-equivalent", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(gbs / hbm, 4) if hbm else None,
+                             "note": "algorithmic bytes of the plain schedule over the cluster decoder's time"}}
+            del r
+        if eb == 2.0:
+            for fp16 in (True, False):
+                kw = dict(max_iters=T, early_stop=False, msg_fp16=fp16, schedule="plain", want_post=False)
+                ws = torch.empty(L.decode_workspace_size(code, F, max_iters=T, msg_fp16=fp16, schedule="plain"),
+                                 dtype=torch.uint8, device=dev)
+                r = L.decode(code, llr, workspace=ws, **kw)
+                ms = _timed_ms(torch, lambda: L.decode(code, llr, workspace=ws, out=r, **kw), reps=3)
+                fe = int((r.hard != 0).any(dim=1).sum())
+                hbm_bytes = F * T * ((6 if fp16 else 12) * E + 12 * n)
+                pt["plain_fp16" if fp16 else "plain_fp32"] = {
+                    "ms": round(ms, 3), "gbps": round(F * k / (ms * 1e-3) / 1e9, 4), "fer": fe / F,
+                    "roofline": {"bound": "hbm", "achieved": round(hbm_bytes / (ms * 1e-3) / 1e9, 1), "peak": hbm,
+                                 "unit": "GB/s", "frac": round(hbm_bytes / (ms * 1e-3) / 1e9 / hbm, 4) if hbm else None}}
+                del r, ws
+            pt["speedup_fp16_cluster_vs_plain_fp32"] = round(pt["plain_fp32"]["ms"] / pt["fp16"]["ms"], 3)
+            pt["fer_equal_within_0.1pct"] = abs(pt["fp16"]["fer"] - pt["plain_fp32"]["fer"]) * F <= 0.001 * F
+        # oracle check on 8 host-generated frames
+        zero = np.zeros((8, n), dtype=np.uint8)
+        hl = S.bpsk_awgn_llr(zero, eb, rate, S.frame_noise(8, n, 3100 + int(eb * 10)))
+        ref = oracle.decode(h, hl, iters=T, nthreads=os.cpu_count() or 1)
+        chk = {"frames": 8, "oracle_fer": float(ref.hard.any(axis=1).mean())}
+        for fp16 in (True, False):
+            r = L.decode(code, torch.from_numpy(hl).to(dev), max_iters=T, msg_fp16=fp16)
+            post = r.post.cpu().numpy()
+            mx, mean = _llr_err(post, ref.post)
+            words = r.hard.cpu().numpy().view(np.uint32)
+            hard = S.unpack_bits(words, n)
+            chk["fp16" if fp16 else "fp32"] = {"max_abs_dL": round(mx, 5), "mean_abs_dL": round(mean, 6),
+                                               "fer": float(hard.any(axis=1).mean()),
+                                               "hard_equal_oracle": float((hard == ref.hard).mean())}
+        pt["oracle_check"] = chk
+        out["points"][f"{eb}dB"] = pt
+        del llr
+    code.close()
+    return out
+
+
+def _random_codewords(L, torch, code, F, g, dev):
+    """F uniform information words encoded by the library: packed words and bits [F, n]."""
+    info = torch.randint(0, 2 ** 32, (F, code.KW), dtype=torch.int64, device=dev, generator=g).to(torch.int32)
+    if code.k % 32:
+        info[:, -1] &= (1 << (code.k % 32)) - 1
+    cw = L.encode(code, info)
+    bits = ((cw.unsqueeze(-1) >> torch.arange(32, device=dev, dtype=torch.int32)) & 1).reshape(F, -1)[:, :code.n]
+    return cw, bits.float()
+
+
+def bench_c4(L, torch, dev, xu_peak):
+    """The mixed serving batch: 2000 frames whose code is drawn uniformly from
+    15 random regular codes (n in {504 .. 8064} x degree pairs (3,6), (3,9),
+    (3,12)), Eb/N0 ~ U[1, 4] dB per frame, early stop after at most 50
+    iterations, binary16 messages, one persistent launch (K6) replayed from a
+    CUDA graph with the autotuned configuration."""
+    import ldpc_synth as S
+    NS = (504, 1008, 2016, 4032, 8064)
+    DEGS = ((3, 6), (3, 9), (3, 12))
+    codes = [L.Code.from_csr_code(S.random_regular(n, dv, dc, seed=40 + 3 * i + j))
+             for i, n in enumerate(NS) for j, (dv, dc) in enumerate(DEGS)]
+    F, T = 2000, 50
+    rng = np.random.default_rng(41)
+    fc = rng.integers(0, len(codes), F).astype(np.int32)
+    ebn0 = rng.uniform(1.0, 4.0, F)
+    plan = L.MixedPlan(codes, msg_fp16=True)
+    b = plan.batch(fc)
+    lo = b.llr_off.cpu().numpy()
+    ho = b.hard_off.cpu().numpy()
+    llr = torch.empty((b.n_llr,), dtype=torch.float32, device=dev)
+    sent = [None] * F
+    g = torch.Generator(device=dev)
+    g.manual_seed(4004)
+    for c, code in enumerate(codes):
+        fr = np.nonzero(fc == c)[0]
+        if fr.size == 0:
+            continue
+        cw, bits = _random_codewords(L, torch, code, fr.size, g, dev)
+        s2 = torch.from_numpy(1.0 / (2 * (code.k / code.n) * 10 ** (ebn0[fr] / 10))).float().to(dev)[:, None]
+        lv = 2.0 * ((2 * bits - 1) + s2.sqrt() * torch.randn(bits.shape, device=dev, generator=g)) / s2
+        cwh = cw.cpu().numpy()
+        for row, f in enumerate(fr):
+            llr[int(lo[f]):int(lo[f]) + code.n] = lv[row]
+            sent[f] = cwh[row]
+    cfg = plan.autotune(b, llr, max_iters=T, early_stop=True, reps=3)
+    out_t = plan.outputs(b, want_post=False)
+    ws = plan.workspace(F)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.decode(b, llr, max_iters=T, early_stop=True, out=out_t, workspace=ws)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.decode(b, llr, max_iters=T, early_stop=True, out=out_t, workspace=ws)
+    ms = _timed_ms(torch, graph.replay, reps=10)
+    iters = out_t.iters.cpu().numpy()
+    hard = out_t.hard.cpu().numpy()
+    errors = sum(int((hard[int(ho[f]):int(ho[f]) + codes[fc[f]].NW] != sent[f]).any()) for f in range(F))
+    bits_info = int(sum(codes[c].k for c in fc))
+    # the syndrome test of z^(t-1) runs inside the check pass of iteration t,
+    # so a frame stopped at iteration t ran t + 1 check passes (t when it ran
+    # all T): MUFU work 3 ops per edge and check pass
+    passes = np.where(iters < T, iters + 1, T)
+    ops = 3.0 * float(sum(codes[fc[f]].nnz * passes[f] for f in range(F)))
+    achieved = ops / (ms * 1e-3) / 1e12
+    for c in codes:
+        c.close()
+    return {"workload": "15 random regular codes, n 504..8064 x (3,6)/(3,9)/(3,12); 2000 frames, Eb/N0 ~ U[1,4] dB, "
+                        "early stop <= 50 iterations, binary16 messages",
+            "ms": round(ms, 4), "gbps": round(bits_info / (ms * 1e-3) / 1e9, 4), "frames": F,
+            "mean_iterations": round(float(iters.mean()), 3), "fer": errors / F, "autotuned": cfg,
+            "graph": "one persistent launch (plus the count, offset and scatter kernels) replayed from a CUDA graph",
+            "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(xu_peak, 4),
+                         "unit": "Tops/s (MUFU ex2/rcp/lg2)", "frac": round(achieved / xu_peak, 4),
+                         "note": "3 MUFU ops per edge and check pass actually run (early stop)"}}
+
+
+def bench_c5(L, torch, dev, peaks):
+    """Differentiable weighted BP: the (3,6) code n = 1008, T = 10 unrolled
+    iterations with one weight per edge and iteration (all 1.0), 4096 frames
+    at 2 dB, binary cross-entropy of the soft outputs against the sent bits;
+    forward with per-iteration checkpoints (K7) and the hand-written adjoint
+    (K8)."""
+    import ldpc_synth as S
+    code = L.Code.from_csr_code(S.random_regular(1008, 3, 6, seed=5))
+    F, T = 4096, 10
+    n, E = code.n, code.nnz
+    g = torch.Generator(device=dev)
+    g.manual_seed(5005)
+    _, bits = _random_codewords(L, torch, code, F, g, dev)
+    s2 = 1.0 / (2 * (code.k / code.n) * 10 ** (2.0 / 10))
+    llr = (2.0 * ((2 * bits - 1) + s2 ** 0.5 * torch.randn(bits.shape, device=dev, generator=g)) / s2).contiguous()
+    w = torch.ones((T, E), dtype=torch.float32, device=dev, requires_grad=True)
+
+    def fwd():
+        return L.WeightedBP.apply(llr, w, code)
+
+    def fwd_bwd():
+        w.grad = None
+        post = L.WeightedBP.apply(llr, w, code)
+        loss = torch.nn.functional.binary_cross_entropy_with_logits(post, bits, reduction="mean")
+        loss.backward()
+
+    with torch.no_grad():
+        f_ms = _timed_ms(torch, fwd, reps=5)
+    fb_ms = _timed_ms(torch, fwd_bwd, reps=5)
+    b_ms = fb_ms - f_ms
+    # algorithmic bytes per frame and iteration (FP32, frame-interleaved):
+    # forward check 8E + 4n (E^{t-1} in, E^t out, L^{t-1} gathered once via
+    # cache), forward bit 4E + 8n; backward bit 12E + 8n, backward check 12E + 4n
+    fwd_bytes = F * T * (12 * E + 12 * n)
+    bwd_bytes = F * T * (24 * E + 12 * n)
+    hbm = peaks.get("hbm_gbs")
+    grad_ok = bool(torch.isfinite(w.grad).all())
+    code.close()
+    return {"workload": f"(3,6) n={n}, T={T}, {F} frames at 2 dB, w = 1, BCE loss",
+            "forward_ms": round(f_ms, 3), "backward_ms": round(b_ms, 3), "forward_backward_ms": round(fb_ms, 3),
+            "checkpoint_mb": round(F * T * (E + n) * 4 / 1e6, 1), "grad_finite": grad_ok,
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+                         "forward_achieved": round(fwd_bytes / (f_ms * 1e-3) / 1e9, 1),
+                         "forward_frac": round(fwd_bytes / (f_ms * 1e-3) / 1e9 / hbm, 4) if hbm else None,
+                         "backward_achieved": round(bwd_bytes / (b_ms * 1e-3) / 1e9, 1),
+                         "backward_frac": round(bwd_bytes / (b_ms * 1e-3) / 1e9 / hbm, 4) if hbm else None,
+                         "note": "algorithmic bytes: forward 12E + 12n, backward 24E + 12n per frame-iteration"}}
 
 
 def run_reference(args):
@@ -667,6 +938,8 @@ def main():
     ap.add_argument("--no-table1", action="store_true",
                     help="skip the paper's Table I workload and the n = 26112 encode comparison")
     ap.add_argument("--ref-frames-per-thread", type=int, default=4)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the quasi-cyclic, mixed-batch and weighted-BP workloads")
     ap.add_argument("--profile-case", choices=["resident", "plain", "cluster", "table1-vector"], default=None,
                     help="run one small decode (for ncu captures) instead of the benchmark")
     ap.add_argument("--frames", type=int, default=4096, help="frames of the --profile-case run")

@@ -297,7 +297,7 @@ int ldpc_wbp_checkpoint_size(const ldpc_code *code, int32_t F, int32_t T, size_t
 
 /* Forward pass: d_llr F x n, d_w T x nnz, d_post F x n receives L^T (natural
  * units).  d_ckpt (>= ldpc_wbp_checkpoint_size bytes, 256-byte aligned) keeps
- * the per-iteration state for the backward pass.  Row degree <= 8, column
+ * the per-iteration state for the backward pass.  Row degree <= 16, column
  * degree <= 32 (LDPC_ENOTSUP otherwise). */
 int ldpc_wbp_forward(const ldpc_code *code, const float *d_llr, int32_t F, int32_t T,
                      const float *d_w, float clip, float *d_post, void *d_ckpt, size_t ckpt_bytes,
@@ -338,6 +338,13 @@ int ldpc_decode_backward(const ldpc_code *code, int32_t F, int32_t T, const floa
 int ldpc_decode_noalloc(const ldpc_code *code, const float *d_llr, int32_t F,
                         const ldpc_decode_opts *opts, float *d_post, uint32_t *d_hard,
                         int32_t *d_iters, uint8_t *d_ok, ldpc_stream_t stream);
+
+/* Test hook, no counterpart in the paper: the device allocation that follows
+ * `after` successful ones fails as if the device were out of memory (once;
+ * a negative value cancels a pending failure).  Every call that allocates
+ * (code creation, encoding tables, mixed plans) then returns LDPC_ENOMEM and
+ * frees what it had taken.  Process-wide; for tests of those error paths. */
+int ldpc_test_fail_allocation(int32_t after);
 
 /* Status code to a static string. */
 const char *ldpc_status_string(int status);

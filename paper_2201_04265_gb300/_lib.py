@@ -50,6 +50,7 @@ SIGNATURES = {
     "ldpc_code_positions": (c_i32, [c_vp, c_vp, c_vp]),
     "ldpc_code_parity_map": (c_i32, [c_vp, c_vp]),
     "ldpc_code_schedule": (c_i32, [c_vp, c_vp, ctypes.POINTER(c_i64)]),
+    "ldpc_test_fail_allocation": (c_i32, [c_i32]),
     "ldpc_code_cluster_shape": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32),
                                         ctypes.POINTER(ctypes.c_float)]),
     "ldpc_code_destroy": (None, [c_vp]),

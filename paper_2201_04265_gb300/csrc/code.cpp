@@ -14,6 +14,23 @@ namespace ldpc {
 
 static thread_local std::string g_last_error;
 
+// Allocations left before the injected failure; < 0: no failure pending.
+static std::atomic<int64_t> g_fail_after{-1};
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    int64_t left = g_fail_after.load();
+    while (left >= 0) {
+        if (g_fail_after.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;  // the injected failure; the hook is spent
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 int fail(int status, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -201,7 +218,7 @@ int build_host(ldpc_code *c) {
 template <class T>
 int upload(T **dst, const T *src, size_t count) {
     if (count == 0) count = 1;  // keep a valid, non-null allocation
-    LDPC_TRY_CUDA(cudaMalloc((void **)dst, count * sizeof(T)));
+    LDPC_TRY_CUDA(dev_malloc((void **)dst, count * sizeof(T)));
     if (src) LDPC_TRY_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
     return LDPC_OK;
 }
@@ -296,6 +313,11 @@ const char *ldpc_status_string(int s) {
 }
 
 const char *ldpc_last_error(void) { return g_last_error.c_str(); }
+
+int ldpc_test_fail_allocation(int32_t after) {
+    g_fail_after.store(after < 0 ? -1 : (int64_t)after);
+    return LDPC_OK;
+}
 
 int ldpc_code_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t *col_idx,
                      const ldpc_qc_desc *qc, uint32_t flags, ldpc_code **out) {

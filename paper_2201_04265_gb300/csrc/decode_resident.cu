@@ -994,7 +994,7 @@ int ldpc_mixed_create(const ldpc_code *const *codes, int32_t ncodes, int32_t msg
         std::vector<uint32_t> tab = build_slot_table(c, sh->dc, sh->cpt, team);
         if (tab.empty()) return cleanup(fail(LDPC_ENOTSUP, "code %d: no slot table for team %d", i, team));
         uint32_t *dt = nullptr;
-        cudaError_t err = cudaMalloc(&dt, sizeof(uint32_t) * tab.size());
+        cudaError_t err = dev_malloc((void **)&dt, sizeof(uint32_t) * tab.size());
         if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMalloc(mixed slot table)"));
         p->tables.push_back(dt);
         err = cudaMemcpy(dt, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice);
@@ -1003,7 +1003,7 @@ int ldpc_mixed_create(const ldpc_code *const *codes, int32_t ncodes, int32_t msg
         p->host_desc.push_back(MixedDesc{c->n, pad_bits(c), sh->dc, team, teams, i, dt});
         p->smem = std::max(p->smem, (size_t)teams * tb);
     }
-    cudaError_t err = cudaMalloc(&p->d_desc, sizeof(MixedDesc) * ncodes);
+    cudaError_t err = dev_malloc((void **)&p->d_desc, sizeof(MixedDesc) * ncodes);
     if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMalloc(mixed descriptors)"));
     int st = upload_order(p, p->cfg.order);
     if (st != LDPC_OK) return cleanup(st);

@@ -332,9 +332,9 @@ int build_encode_tables(ldpc_code *c, size_t *bytes) {
     const int64_t total = NS * NG * 256;  // table rows of 4 words
     const size_t tab_bytes = (size_t)total * kM4Slice * sizeof(uint32_t);
     uint32_t *AC = nullptr, *tab = nullptr;
-    cudaError_t e = cudaMalloc((void **)&AC, (size_t)I8 * RWp * sizeof(uint32_t));
+    cudaError_t e = dev_malloc((void **)&AC, (size_t)I8 * RWp * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(LDPC_ENOMEM, "column table allocation: %s", cudaGetErrorString(e));
-    e = cudaMalloc((void **)&tab, tab_bytes);
+    e = dev_malloc((void **)&tab, tab_bytes);
     if (e != cudaSuccess) {
         cudaFree(AC);
         return fail(LDPC_ENOMEM, "table allocation (%zu bytes): %s", tab_bytes, cudaGetErrorString(e));

@@ -29,6 +29,11 @@ int cuda_fail(cudaError_t err, const char *what);
         if (_s != LDPC_OK) return _s; \
     } while (0)
 
+// Every device allocation of the library goes through here, so that a test
+// can make one fail on the host (ldpc_test_fail_allocation) and check that the
+// caller returns LDPC_ENOMEM and frees what it took.
+cudaError_t dev_malloc(void **p, size_t bytes);
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // The message clip in the kernels' log2 units.

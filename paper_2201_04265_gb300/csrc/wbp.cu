@@ -36,7 +36,7 @@ namespace ldpc {
 namespace {
 
 constexpr int kWFB = 128;  // frames (threads) per block
-constexpr int kWMaxDeg = 8;
+constexpr int kWMaxDeg = 16;  // widest row: instances for rows of <= 8, <= 12 and <= 16 edges
 constexpr int kWMaxCol = 32;  // column weight bound of the backward bit kernel
 
 struct WbpCkpt {
@@ -374,8 +374,15 @@ int ldpc_wbp_forward(const ldpc_code *c, const float *d_llr, int32_t F, int32_t 
         float *Ecur = ck.E + (t - 1) * eF;
         float *Lcur = ck.L + (t - 1) * nF;
         const dim3 cg((unsigned)c->m, (unsigned)ceil_div(F, kWFB));
-        wbp_check<kWMaxDeg><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, Ecur, c->d.row_ptr, c->d.eval_col,
-                                                c->d.eval_edge, c->m, F, ck.Fs, clip2);
+        if (c->dc_max <= 8)
+            wbp_check<8><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, Ecur, c->d.row_ptr, c->d.eval_col,
+                                             c->d.eval_edge, c->m, F, ck.Fs, clip2);
+        else if (c->dc_max <= 12)
+            wbp_check<12><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, Ecur, c->d.row_ptr, c->d.eval_col,
+                                              c->d.eval_edge, c->m, F, ck.Fs, clip2);
+        else
+            wbp_check<16><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, Ecur, c->d.row_ptr, c->d.eval_col,
+                                              c->d.eval_edge, c->m, F, ck.Fs, clip2);
         const dim3 bg((unsigned)c->n, (unsigned)ceil_div(F, kWFB));
         wbp_bit<<<bg, kWFB, 0, s>>>(ck.Rt, Ecur, d_w + (size_t)(t - 1) * c->nnz, Lcur, c->d.col_ptr,
                                     c->d.col_edge, c->d.col_pos, c->n, F, ck.Fs);
@@ -438,8 +445,15 @@ int ldpc_decode_backward(const ldpc_code *c, int32_t F, int32_t T, const float *
         const float *Lprev = t == 1 ? ck.Rt : ck.L + (t - 2) * nF;
         const float *Eprev = t == 1 ? nullptr : ck.E + (t - 2) * eF;
         const float *wprev = t == 1 ? nullptr : d_w + (size_t)(t - 2) * c->nnz;
-        wbp_check_back<kWMaxDeg><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, wk.gE, gX, c->d.row_ptr,
-                                                     c->d.eval_col, c->d.eval_edge, c->m, F, ck.Fs, clip2);
+        if (c->dc_max <= 8)
+            wbp_check_back<8><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, wk.gE, gX, c->d.row_ptr,
+                                                  c->d.eval_col, c->d.eval_edge, c->m, F, ck.Fs, clip2);
+        else if (c->dc_max <= 12)
+            wbp_check_back<12><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, wk.gE, gX, c->d.row_ptr,
+                                                   c->d.eval_col, c->d.eval_edge, c->m, F, ck.Fs, clip2);
+        else
+            wbp_check_back<16><<<cg, kWFB, 0, s>>>(Lprev, Eprev, wprev, wk.gE, gX, c->d.row_ptr,
+                                                   c->d.eval_col, c->d.eval_edge, c->m, F, ck.Fs, clip2);
     }
     wbp_final_r<<<bg, kWFB, 0, s>>>(gX, wk.gR, c->d.col_ptr, c->d.col_pos, c->n, F, ck.Fs);
     if (d_grad_llr)

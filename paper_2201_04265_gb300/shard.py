@@ -22,6 +22,7 @@ all-reduce of the weight gradient (``allreduce_mean_``), outside decoding.
 
 from __future__ import annotations
 
+from datetime import timedelta
 from typing import Callable
 
 import numpy as np
@@ -97,6 +98,41 @@ def run_sharded(l: int, work: Callable[[int, int], dict], group=None,
         g = gatherv(out[key], l, group=group, dst=dst)
         res[key] = g
     return res if rank == dst else None
+
+
+class PeerLost(RuntimeError):
+    """A process of the replica group did not reach a step in time."""
+
+
+def step_barrier(store, step: int, timeout_s: float, group=None) -> None:
+    """Host-side liveness check between steps (no counterpart in the paper,
+    whose MPI processes are assumed to survive).  Every process announces
+    ``step`` in the key-value ``store`` and waits, at most ``timeout_s``
+    seconds, for all others to do the same; it raises ``PeerLost`` naming the
+    processes that did not arrive.  It runs between steps, when no device work
+    or collective of this process is in flight, so a process that exited or
+    hung is found before the next gather is started rather than inside it."""
+    rank, N = _world(group)
+    store.set(f"ldpc-step/{step}/{rank}", "1")
+    keys = [f"ldpc-step/{step}/{q}" for q in range(N)]
+    try:
+        store.wait(keys, timedelta(seconds=timeout_s))
+    except Exception as exc:  # the store's own timeout error
+        missing = [q for q in range(N) if not store.check([keys[q]])]
+        raise PeerLost(f"processes {missing} did not reach step {step} within {timeout_s} s") from exc
+
+
+def run_sharded_steps(steps: int, l: int, work: Callable[[int, int, int], dict], store, timeout_s: float,
+                      group=None, dst: int = 0) -> list:
+    """``steps`` rounds of ``run_sharded``, each preceded by ``step_barrier``:
+    ``work(step, f0, f1)`` decodes this process's block of step ``step``.
+    Returns the gathered results of every step on ``dst`` (None elsewhere);
+    raises ``PeerLost`` when a process is missing at a step boundary."""
+    out = []
+    for step in range(steps):
+        step_barrier(store, step, timeout_s, group=group)
+        out.append(run_sharded(l, lambda f0, f1, s=step: work(s, f0, f1), group=group, dst=dst))
+    return out
 
 
 def allreduce_mean_(t: torch.Tensor, l: int | None = None, group=None) -> torch.Tensor:

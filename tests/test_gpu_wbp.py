@@ -130,3 +130,80 @@ def test_backward_deterministic_and_zero_iterations(L):
     np.testing.assert_array_equal(post.detach().cpu().numpy(), wl.llr)
     post.sum().backward()
     assert torch.all(llr_t.grad == 1)
+
+
+def _check_grads(got_ref_pairs):
+    for got, ref in got_ref_pairs:
+        cos = float(np.dot(got.ravel(), ref.ravel()) / (np.linalg.norm(got) * np.linalg.norm(ref)))
+        assert cos >= 0.9999, cos
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+        mx = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-5 * mx
+        big = np.abs(ref) >= 1e-3 * mx
+        rel = np.abs(got[big] - ref[big]) / np.abs(ref[big])
+        assert rel.max() <= 1e-3, rel.max()
+
+
+def test_backward_at_256_frames_against_fp64_reference_and_finite_differences(L):
+    """The gradient bar at 256 frames of the configuration-5 code (n = 1008,
+    T = 10, 2 dB): against the FP64 autograd reference, and central finite
+    differences (h = 1e-3) of the GPU forward on the 24 largest coordinates."""
+    wl = workload("reg36_1008", 256, 2.0, seed=90)
+    c = dev_code(L, "reg36_1008")
+    T = 10
+    wts = _weights(T, c.nnz, seed=91)
+    loss, gw, gR = _gpu_loss_grads(L, c, wl.llr, wts, wl.cw)
+    rloss, rgw, rgR, _ = wbp_ref.loss_and_grads(wl.code, wl.llr.astype(np.float64), wts.astype(np.float64), wl.cw)
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss) + 1e-7
+    _check_grads(((gw, rgw), (gR, rgR)))
+    bits = torch.from_numpy(wl.cw.astype(np.float32)).cuda()
+    llr_t = torch.from_numpy(wl.llr).cuda()
+
+    def loss_of(wv):
+        post = L.weighted_bp(c, llr_t, torch.from_numpy(wv).cuda())
+        return float(torch.nn.functional.binary_cross_entropy_with_logits(post.double(), bits.double(),
+                                                                          reduction="mean"))
+
+    h = 1e-3
+    for flat in np.argsort(-np.abs(gw).ravel())[:24]:
+        t, e = divmod(int(flat), c.nnz)
+        wp = wts.copy(); wp[t, e] += h
+        wm = wts.copy(); wm[t, e] -= h
+        fd = (loss_of(wp) - loss_of(wm)) / (2 * h)
+        assert abs(fd - gw[t, e]) <= 2e-2 * abs(gw[t, e]) + 1e-7, (t, e, fd, gw[t, e])
+
+
+def test_backward_deterministic_at_4096_frames(L):
+    """The configuration-5 batch (4096 frames, T = 10): two backward passes
+    give identical weight and input gradients (fixed-order frame reduction)."""
+    wl = workload("reg36_1008", 4096, 2.0, seed=92)
+    c = dev_code(L, "reg36_1008")
+    wts = _weights(10, c.nnz, seed=93)
+    a = _gpu_loss_grads(L, c, wl.llr, wts, wl.cw)
+    b = _gpu_loss_grads(L, c, wl.llr, wts, wl.cw)
+    assert a[0] == b[0]
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[2], b[2])
+    assert np.isfinite(a[1]).all() and np.abs(a[1]).max() > 0
+
+
+def test_table1_code_rows_of_12(L):
+    """The paper's Table I code of rate 1/2 (rows of 12 ones): unit weights give
+    the plain decoder's bits, random weights the oracle's forward, and the
+    adjoint the FP64 reference gradient."""
+    wl = workload("table1_r050", 24, 3.0, seed=94)
+    c = dev_code(L, "table1_r050")
+    llr = torch.from_numpy(wl.llr).cuda()
+    post = L.weighted_bp(c, llr, torch.ones((6, c.nnz), dtype=torch.float32, device="cuda"))
+    ref = L.decode(c, llr, max_iters=6, schedule="plain")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(post.cpu().numpy(), ref.post.cpu().numpy())
+    T = 3
+    wts = _weights(T, c.nnz, seed=95)
+    post = L.weighted_bp(c, llr, torch.from_numpy(wts).cuda())
+    oref = oracle.decode(wl.code, wl.llr, iters=T, weights=wts.astype(np.float64))
+    assert llr_close(post.cpu().numpy(), oref.post).all()
+    loss, gw, gR = _gpu_loss_grads(L, c, wl.llr, wts, wl.cw)
+    rloss, rgw, rgR, _ = wbp_ref.loss_and_grads(wl.code, wl.llr.astype(np.float64), wts.astype(np.float64), wl.cw)
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss) + 1e-7
+    _check_grads(((gw, rgw), (gR, rgR)))

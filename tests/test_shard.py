@@ -79,3 +79,26 @@ def test_gloo_two_process_gather_equals_whole_batch(tmp_path, l):
     c0, c1 = shard.num_elems(0, 2, l), shard.num_elems(1, 2, l)
     np.testing.assert_allclose(got["g"], np.full((3, 5), (c0 + 2 * c1) / l))
     np.testing.assert_allclose(got["h"], np.full(4, 1.5))
+
+
+def test_lost_peer_is_reported_at_the_next_step(tmp_path):
+    """Process 1 leaves after the first step; process 0 finishes that step's
+    gather, then reports PeerLost naming process 1 at the second step's
+    boundary within its 1 s limit, instead of hanging in a collective."""
+    import shard_worker
+    out = str(tmp_path / "lost.pkl")
+    mp.start_processes(shard_worker.run_with_lost_peer, args=(2, _free_port(), _free_port(), 6, out), nprocs=2,
+                       join=True, start_method="spawn")
+    got = pickle.load(open(out, "rb"))
+    assert got["steps_done"] == 1
+    assert got["error"] is not None and "[1]" in got["error"] and "step 1" in got["error"]
+    assert got["seconds"] < 20
+
+
+def test_step_barrier_single_process():
+    import datetime
+    import torch.distributed as dist
+    store = dist.HashStore()
+    shard.step_barrier(store, 0, timeout_s=0.1)   # no process group: one process, nothing to wait for
+    assert store.check(["ldpc-step/0/0"])
+    del datetime
