@@ -329,18 +329,20 @@ def run_ours(args):
             e_ms = float(te.item())
         enc_ms = [m[0].elapsed_time(m[1]) for m in marks]
         hdec_ms = [m[1].elapsed_time(m[2]) for m in marks]
-        # one more pass with a record of every chunk (outside the timed steps):
-        # where the time goes between the host link and the decoder
-        _, tl = hdec.decode_timeline(host_llr[0], out=hout)
-        timeline = {"chunks": int(tl.shape[0]), "chunk_frames": 8192,
-                    "upload_ms": [round(float(x), 2) for x in tl[:, 1] - tl[:, 0]],
-                    "decode_ms": [round(float(x), 2) for x in tl[:, 3] - tl[:, 2]],
-                    "download_ms": [round(float(x), 2) for x in tl[:, 5] - tl[:, 4]],
-                    "decoder_idle_ms": [round(float(tl[i, 2] - (tl[i - 1, 3] if i else 0.0)), 2)
-                                        for i in range(tl.shape[0])],
-                    "total_ms": round(float(tl[-1, 5]), 2),
-                    "upload_gbs": round(float(host_llr[0][:8192].numel() * 4 / (np.median(tl[:, 1] - tl[:, 0]) * 1e-3)
-                                              / 1e9), 1)}
+        # three more passes with a record of every chunk (outside the timed
+        # steps): where the time goes between the host link and the decoder,
+        # and how much it varies from pass to pass
+        timeline = []
+        for i in range(3):
+            _, tl = hdec.decode_timeline(host_llr[i % len(EBN0)], out=hout)
+            up = tl[:, 1] - tl[:, 0]
+            timeline.append({"total_ms": round(float(tl[-1, 5]), 2),
+                             "upload_ms": [round(float(x), 2) for x in up],
+                             "decode_ms": [round(float(x), 2) for x in tl[:, 3] - tl[:, 2]],
+                             "download_ms": [round(float(x), 2) for x in tl[:, 5] - tl[:, 4]],
+                             "decoder_idle_ms": [round(float(tl[j, 2] - (tl[j - 1, 3] if j else 0.0)), 2)
+                                                 for j in range(tl.shape[0])],
+                             "upload_gbs_median": round(float(8192 * code.n * 4 / (np.median(up) * 1e-3) / 1e9), 1)})
         h2d = host_llr[0].numel() * 4 + host_info.numel() * 4
         d2h = host_cw.numel() * 4 + hout.hard.numel() * 4 + hout.iters.numel() * 4 + hout.ok.numel()
         e2e = {"value": round(world * bits_per_step / (e_ms * 1e-3) / 1e9, 4), "unit": "Gbit/s",

@@ -228,8 +228,11 @@ plain_check(const float *__restrict__ Lt, MsgT *__restrict__ Et,
 // Check-node update for rows wider than 32 (one frame per thread): inputs are
 // combined in chunks of 8; a first pass forms each chunk's pair, a second pass
 // reloads each chunk's inputs and combines the within-chunk leave-one-out pair
-// with the pairs of all other chunks.  Rows up to 8 * kMaxChunks wide.
+// with the pairs of all other chunks.  Rows up to 8 * kMaxChunks wide.  The
+// chunk pairs and their prefixes are kept in shared memory ([4][chunk][thread]
+// floats, so a warp's accesses hit 32 banks), not in registers.
 constexpr int kMaxChunks = 32;
+constexpr size_t kWideSmem = sizeof(float) * 4 * kMaxChunks * kFB;
 
 template <class MsgT>
 __global__ void __launch_bounds__(kFB)
@@ -238,8 +241,11 @@ plain_check_wide(const float *__restrict__ Lt, MsgT *__restrict__ Et,
                  const int32_t *__restrict__ rows, const int32_t *__restrict__ stop_it,
                  uint32_t *__restrict__ unsat, int32_t mc, int32_t F, int64_t Fs, float clip2,
                  int first, int check_syndrome) {
+    extern __shared__ float wide_pairs[];  // [4][kMaxChunks][kFB]: ch.e, ch.o, preC.e, preC.o
     const int64_t f = (int64_t)blockIdx.y * kFB + threadIdx.x;
     if (f >= F || stop_it[f] >= 0) return;
+    float *ch_e = wide_pairs + threadIdx.x, *ch_o = ch_e + kMaxChunks * kFB;
+    float *pre_e = ch_o + kMaxChunks * kFB, *pre_o = pre_e + kMaxChunks * kFB;
     uint32_t bad = 0;
     for (int cc = 0; cc < kCPB; ++cc) {
         const int ci = blockIdx.x * kCPB + cc;
@@ -248,10 +254,8 @@ plain_check_wide(const float *__restrict__ Lt, MsgT *__restrict__ Et,
         const int e0 = __ldg(&row_ptr[c]);
         const int d = __ldg(&row_ptr[c + 1]) - e0;
         const int nch = (d + 7) >> 3;
-        EvOd ch[kMaxChunks], preC[kMaxChunks];
         uint32_t sall = (uint32_t)d & 1u, zpar = 0;
         EvOd run = {1.f, 0.f};
-#pragma unroll
         for (int k = 0; k < kMaxChunks; ++k) {
             if (k < nch) {
                 EvOd p = {1.f, 0.f};
@@ -267,17 +271,18 @@ plain_check_wide(const float *__restrict__ Lt, MsgT *__restrict__ Et,
                     sall ^= __float_as_uint(x) >> 31;
                     p = evod_add(p, check_u(x));
                 }
-                ch[k] = p;
-                preC[k] = run;
+                ch_e[k * kFB] = p.e;
+                ch_o[k * kFB] = p.o;
+                pre_e[k * kFB] = run.e;
+                pre_o[k * kFB] = run.o;
                 run = evod_join(run, p);
             }
         }
         bad |= zpar;
         EvOd sufC = {1.f, 0.f};
-#pragma unroll
         for (int k = kMaxChunks - 1; k >= 0; --k) {
             if (k < nch) {
-                const EvOd other = evod_join(preC[k], sufC);
+                const EvOd other = evod_join(EvOd{pre_e[k * kFB], pre_o[k * kFB]}, sufC);
                 const int jn = min(8, d - 8 * k);
                 float u[8];
                 uint32_t sm = 0;
@@ -307,7 +312,7 @@ plain_check_wide(const float *__restrict__ Lt, MsgT *__restrict__ Et,
                         suf = evod_add(suf, u[jj]);
                     }
                 }
-                sufC = evod_join(ch[k], sufC);
+                sufC = evod_join(EvOd{ch_e[k * kFB], ch_o[k * kFB]}, sufC);
             }
         }
     }
@@ -479,7 +484,8 @@ int run_plain(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_deco
             default: {
                 const int32_t r0 = c->row_class[q], mc = c->row_class[q + 1] - r0;
                 dim3 grid((unsigned)ceil_div(mc, kCPB), (unsigned)ceil_div(F, kFB));
-                plain_check_wide<MsgT><<<grid, kFB, 0, s>>>(
+                LDPC_TRY(kernel_setup((const void *)plain_check_wide<MsgT>, kFB, kWideSmem, nullptr));
+                plain_check_wide<MsgT><<<grid, kFB, kWideSmem, s>>>(
                     ws.Lt, static_cast<MsgT *>(ws.Et), c->d.row_ptr, c->d.eval_col, c->d.row_order + r0,
                     ws.stop_it, u_cur, mc, F, ws.Fs, clip2, first, check_syn);
             }
