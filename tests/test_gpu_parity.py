@@ -242,14 +242,15 @@ def test_decode_fp16_storage_llr_error_at_1_5db(L):
     pinned by design, so this states the error and gates it on what binary16
     rounding allows -- the mean clipped |dL| stays below 1e-2 and the hard
     decisions of every frame the oracle decodes agree.  Measured on GB300 for
-    the n = 8064 code at the same point: max 0.13, mean 4e-4."""
+    the n = 8064 code at the same point: max 0.13, mean 4e-4; for this code max 9.1
+    (a frame that does not converge), mean 7e-3."""
     w = workload("reg36_1008", 400, 1.5, seed=62)
     c = dev_code(L, "reg36_1008")
     post, hard, iters, ok = _gpu_decode(L, c, w.llr, max_iters=50, schedule="resident", msg_fp16=True)
     ref = oracle.decode(w.code, w.llr, iters=50, nthreads=16)
     err = np.abs(np.clip(post.astype(np.float64), -20, 20) - np.clip(ref.post, -20, 20))
     print(f"binary16 messages, n=1008 at 1.5 dB: max |dL| {err.max():.4g}, mean {err.mean():.4g}, "
-          f"oracle FER {ref.hard.any(axis=1).mean():.3f}")
+          f"oracle FER {(ref.hard != w.cw).any(axis=1).mean():.3f}")
     assert 0 < ref.ok.mean() < 1          # an informative point: some frames fail
     assert err.mean() < 1e-2
     good = ref.ok.astype(bool)            # frames near the threshold may flip under binary16 rounding
