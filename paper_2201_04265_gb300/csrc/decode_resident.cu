@@ -819,6 +819,68 @@ __global__ void mixed_scatter(const int32_t *__restrict__ frame_code, int32_t F,
     sorted[start[c] + atomicAdd(&fill[c], 1u)] = (int32_t)f;
 }
 
+// Channel quality of each frame: the mean |R_v| of its first (up to) 1024
+// bits (for BPSK over AWGN it grows with Eb/N0), one warp per frame.  Frames of
+// poor quality are the ones likely to run every iteration.
+__global__ void mixed_score(const int32_t *__restrict__ frame_code, const int64_t *__restrict__ llr_off,
+                            const float *__restrict__ llr, const int32_t *__restrict__ nbits, int32_t F,
+                            int32_t ncodes, float *__restrict__ score) {
+    const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (f >= F) return;
+    const int c = frame_code[f];
+    if (c < 0 || c >= ncodes) return;
+    const int n = min(nbits[c], 1024);
+    const float *x = llr + llr_off[f];
+    float sum = 0.f;
+#pragma unroll 8
+    for (int v = lane; v < n; v += 32) sum += fabsf(x[v]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) score[f] = sum / (float)n;
+}
+
+// Orders each code's bucket by channel quality, poorest first (ties by frame
+// index), one CTA per code: a frame's rank is the number of frames before it.
+// The work items then start with the frame groups most likely to run every
+// iteration, and the two frames of a binary16 group have similar quality, so a
+// group rarely waits for one slow frame.  The order changes no result.
+constexpr int kSortCap = 4096;  // larger buckets keep their arrival order
+__global__ void __launch_bounds__(512) mixed_sort(const unsigned *__restrict__ start,
+                                                  const unsigned *__restrict__ count,
+                                                  const float *__restrict__ score, int32_t *__restrict__ sorted) {
+    __shared__ float ks[kSortCap];
+    __shared__ int32_t kf[kSortCap];
+    const int c = blockIdx.x;
+    const unsigned n = count[c], st = start[c];
+    if (n < 2 || n > kSortCap) return;
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        kf[i] = sorted[st + i];
+        ks[i] = score[kf[i]];
+    }
+    __syncthreads();
+    int32_t out[kSortCap / 512];
+    unsigned rank[kSortCap / 512];
+#pragma unroll
+    for (int r = 0; r < kSortCap / 512; ++r) {
+        const unsigned i = threadIdx.x + 512u * r;
+        rank[r] = 0;
+        out[r] = -1;
+        if (i < n) {
+            const float si = ks[i];
+            const int32_t fi = kf[i];
+            unsigned k = 0;
+            for (unsigned j = 0; j < n; ++j) k += (ks[j] < si) || (ks[j] == si && kf[j] < fi);
+            rank[r] = k;
+            out[r] = fi;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortCap / 512; ++r)
+        if (out[r] >= 0) sorted[st + rank[r]] = out[r];
+}
+
 // Not inlined: each row shape gets its own register allocation instead of
 // the union of all three inside one kernel body.
 template <int G>
@@ -905,6 +967,7 @@ struct ldpc_mixed {
     std::vector<ldpc::MixedDesc> host_desc;   // in code order
     std::vector<uint32_t *> tables;           // device slot tables, per code
     ldpc::MixedDesc *d_desc = nullptr;        // device, in work order
+    int32_t *d_nbits = nullptr;               // device, n of each code (by code index)
     size_t smem = 0;
     ldpc_mixed_config cfg{0, 1, 1};
     int32_t desc_order = -1;                  // cfg.order the device array holds
@@ -927,6 +990,7 @@ int upload_order(ldpc_mixed *p, int32_t order) {
 struct MixedWs {
     unsigned *count, *fill, *start, *item_off, *counter;
     int32_t *sorted;
+    float *score;
 };
 
 size_t mixed_layout(int32_t ncodes, int32_t F, MixedWs *w, void *base) {
@@ -942,6 +1006,7 @@ size_t mixed_layout(int32_t ncodes, int32_t F, MixedWs *w, void *base) {
     const size_t oI = take(sizeof(unsigned) * (ncodes + 1));
     const size_t oK = take(sizeof(unsigned));
     const size_t oX = take(sizeof(int32_t) * std::max(F, 1));
+    const size_t oQ = take(sizeof(float) * std::max(F, 1));
     if (w && base) {
         char *b = static_cast<char *>(base);
         w->count = reinterpret_cast<unsigned *>(b + oC);
@@ -950,6 +1015,7 @@ size_t mixed_layout(int32_t ncodes, int32_t F, MixedWs *w, void *base) {
         w->item_off = reinterpret_cast<unsigned *>(b + oI);
         w->counter = reinterpret_cast<unsigned *>(b + oK);
         w->sorted = reinterpret_cast<int32_t *>(b + oX);
+        w->score = reinterpret_cast<float *>(b + oQ);
     }
     return off;
 }
@@ -1005,6 +1071,14 @@ int ldpc_mixed_create(const ldpc_code *const *codes, int32_t ncodes, int32_t msg
     }
     cudaError_t err = dev_malloc((void **)&p->d_desc, sizeof(MixedDesc) * ncodes);
     if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMalloc(mixed descriptors)"));
+    err = dev_malloc((void **)&p->d_nbits, sizeof(int32_t) * ncodes);
+    if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMalloc(mixed code sizes)"));
+    {
+        std::vector<int32_t> nb(ncodes);
+        for (int32_t i = 0; i < ncodes; ++i) nb[i] = codes[i]->n;
+        err = cudaMemcpy(p->d_nbits, nb.data(), sizeof(int32_t) * ncodes, cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMemcpy(mixed code sizes)"));
+    }
     int st = upload_order(p, p->cfg.order);
     if (st != LDPC_OK) return cleanup(st);
     *out = p;
@@ -1015,6 +1089,7 @@ void ldpc_mixed_destroy(ldpc_mixed *p) {
     if (!p) return;
     for (uint32_t *t : p->tables) cudaFree(t);
     if (p->d_desc) cudaFree(p->d_desc);
+    if (p->d_nbits) cudaFree(p->d_nbits);
     delete p;
 }
 
@@ -1066,6 +1141,9 @@ int ldpc_decode_mixed(const ldpc_mixed *p, const int32_t *d_frame_code, const in
     mixed_offsets<<<1, 32, 0, s>>>(w.count, p->d_desc, p->ncodes, G, p->cfg.groups_per_item, w.start,
                                    w.item_off, w.fill);
     mixed_scatter<<<fb, 256, 0, s>>>(d_frame_code, F, p->ncodes, w.start, w.fill, w.sorted);
+    mixed_score<<<(unsigned)ceil_div(F, 8), 256, 0, s>>>(d_frame_code, d_llr_off, d_llr, p->d_nbits, F, p->ncodes,
+                                                          w.score);
+    mixed_sort<<<(unsigned)p->ncodes, 512, 0, s>>>(w.start, w.count, w.score, w.sorted);
     const bool syn = early_stop && max_iters >= 2;
     MixedFn fn = pick_mixed(p->fp16, syn);
     int sms = 0, per_sm = 0;
