@@ -92,6 +92,7 @@ extern "C" {
 
 int ldpc_encode(const ldpc_code *c, const uint32_t *d_info, uint32_t *d_code, int32_t F,
                 ldpc_stream_t stream) {
+    TraceRange trace_("ldpc_encode");
     LDPC_TRY(check_code(c));
     if (F < 0) return fail(LDPC_EINVAL, "F < 0");
     if (F == 0) return LDPC_OK;
@@ -112,6 +113,7 @@ int ldpc_encode_tables_free(ldpc_code *c) {
 
 int ldpc_syndrome(const ldpc_code *c, const uint32_t *d_bits, int32_t F, uint32_t *d_syn,
                   uint8_t *d_ok, ldpc_stream_t stream) {
+    TraceRange trace_("ldpc_syndrome");
     LDPC_TRY(check_code(c));
     if (F < 0) return fail(LDPC_EINVAL, "F < 0");
     if (F == 0 || (!d_syn && !d_ok)) return LDPC_OK;
@@ -134,6 +136,7 @@ int ldpc_decode_workspace_size(const ldpc_code *c, int32_t F, const ldpc_decode_
 int ldpc_decode(const ldpc_code *c, const float *d_llr, int32_t F, const ldpc_decode_opts *o,
                 float *d_post, uint32_t *d_hard, int32_t *d_iters, uint8_t *d_ok, void *d_work,
                 size_t work_bytes, ldpc_stream_t stream) {
+    TraceRange trace_("ldpc_decode");
     LDPC_TRY(check_code(c));
     LDPC_TRY(check_opts(o));
     if (F < 0) return fail(LDPC_EINVAL, "F < 0");

@@ -54,6 +54,7 @@ using namespace ldpc;
 extern "C" int ldpc_decode_noalloc(const ldpc_code *c, const float *d_llr, int32_t F,
                                    const ldpc_decode_opts *o, float *d_post, uint32_t *d_hard,
                                    int32_t *d_iters, uint8_t *d_ok, ldpc_stream_t stream) {
+    TraceRange trace_("ldpc_decode_noalloc");
     if (!c) return fail(LDPC_EINVAL, "code is NULL");
     if (!c->on_device) return fail(LDPC_EINVAL, "code was created host-only");
     if (!o) return fail(LDPC_EINVAL, "opts is NULL");

@@ -1120,6 +1120,7 @@ int ldpc_decode_mixed(const ldpc_mixed *p, const int32_t *d_frame_code, const in
                       int32_t early_stop, float clip, float *d_post, uint32_t *d_hard,
                       int32_t *d_iters, uint8_t *d_ok, void *d_work, size_t work_bytes,
                       ldpc_stream_t stream) {
+    TraceRange trace_("ldpc_decode_mixed");
     if (!p) return fail(LDPC_EINVAL, "plan is NULL");
     if (F < 0 || max_iters < 0 || !(clip > 0.f)) return fail(LDPC_EINVAL, "bad F, max_iters or clip");
     if (early_stop != 0 && early_stop != 1) return fail(LDPC_EINVAL, "early_stop must be 0 or 1");
@@ -1179,6 +1180,7 @@ int ldpc_mixed_autotune(ldpc_mixed *p, const int32_t *d_frame_code, const int64_
                         int32_t early_stop, float clip, float *d_post, uint32_t *d_hard,
                         int32_t *d_iters, uint8_t *d_ok, void *d_work, size_t work_bytes,
                         int32_t reps, ldpc_stream_t stream, ldpc_mixed_config *chosen) {
+    TraceRange trace_("ldpc_mixed_autotune");
     if (!p || reps < 1) return fail(LDPC_EINVAL, "bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
     const ldpc_mixed_config start = p->cfg;

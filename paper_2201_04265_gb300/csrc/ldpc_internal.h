@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <climits>
 #include <cstdint>
@@ -33,6 +34,30 @@ int cuda_fail(cudaError_t err, const char *what);
 // can make one fail on the host (ldpc_test_fail_allocation) and check that the
 // caller returns LDPC_ENOMEM and frees what it took.
 cudaError_t dev_malloc(void **p, size_t bytes);
+
+// A named range on the host timeline for profilers (NVTX, domain "ldpc"):
+// each entry point that queues work marks its span, so a timeline shows
+// which call issued which kernels.  Costs nothing when no tool is attached.
+class TraceRange {
+   public:
+    explicit TraceRange(const char *name) {
+        nvtxEventAttributes_t a = {};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        nvtxDomainRangePushEx(domain(), &a);
+    }
+    ~TraceRange() { nvtxDomainRangePop(domain()); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+
+   private:
+    static nvtxDomainHandle_t domain() {
+        static nvtxDomainHandle_t d = nvtxDomainCreateA("ldpc");
+        return d;
+    }
+};
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }

@@ -185,6 +185,7 @@ extern "C" {
 int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ldpc_decode_opts *o,
                      float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
                      void *d_work, size_t work_bytes, ldpc_stream_t stream) {
+    TraceRange trace_("ldpc_decode_host");
     return host_pipeline(c, h_llr, F, o, h_post, h_hard, h_iters, h_ok, chunk, d_work, work_bytes, stream,
                          nullptr);
 }
@@ -192,6 +193,7 @@ int ldpc_decode_host(const ldpc_code *c, const float *h_llr, int32_t F, const ld
 int ldpc_decode_host_timeline(const ldpc_code *c, const float *h_llr, int32_t F, const ldpc_decode_opts *o,
                               float *h_post, uint32_t *h_hard, int32_t *h_iters, uint8_t *h_ok, int32_t chunk,
                               void *d_work, size_t work_bytes, ldpc_stream_t stream, float *h_ms) {
+    TraceRange trace_("ldpc_decode_host_timeline");
     if (!h_ms) return fail(LDPC_EINVAL, "h_ms is NULL");
     if (F <= 0 || chunk < 1) return fail(LDPC_EINVAL, "need F >= 1 and chunk >= 1");
     const int64_t nchunks = ceil_div(F, chunk);

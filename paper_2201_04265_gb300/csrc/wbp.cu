@@ -356,6 +356,7 @@ int ldpc_wbp_checkpoint_size(const ldpc_code *c, int32_t F, int32_t T, size_t *b
 int ldpc_wbp_forward(const ldpc_code *c, const float *d_llr, int32_t F, int32_t T, const float *d_w,
                      float clip, float *d_post, void *d_ckpt, size_t ckpt_bytes,
                      ldpc_stream_t stream) {
+    TraceRange trace_("ldpc_wbp_forward");
     LDPC_TRY(check_wbp_args(c, F, T, clip));
     if (F == 0) return LDPC_OK;
     if (!d_llr || !d_post || !d_ckpt || (T > 0 && !d_w)) return fail(LDPC_EINVAL, "NULL pointer");
@@ -407,6 +408,7 @@ int ldpc_decode_backward(const ldpc_code *c, int32_t F, int32_t T, const float *
                          const void *d_ckpt, size_t ckpt_bytes,
                          const float *d_grad_post, float *d_grad_w, float *d_grad_llr, void *d_work,
                          size_t work_bytes, ldpc_stream_t stream) {
+    TraceRange trace_("ldpc_decode_backward");
     LDPC_TRY(check_wbp_args(c, F, T, clip));
     cudaStream_t s = (cudaStream_t)stream;
     if (T > 0 && d_grad_w && F == 0)
