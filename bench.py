@@ -903,6 +903,16 @@ def run_profile_case(args):
     import ldpc_synth as S
     import paper_2201_04265_gb300 as L
     torch.cuda.set_device(0)
+    if args.profile_case == "wbp":
+        # configuration 5: weighted BP, n = 1008, 4096 frames, T = 10, one
+        # forward and one backward pass after a warm-up pass
+        c5 = bench_c5(L, torch, torch.device("cuda", 0), _peaks()[0])
+        print(json.dumps({"profile_case": "wbp", "forward_ms": c5["forward_ms"], "backward_ms": c5["backward_ms"]}))
+        return
+    if args.profile_case == "mixed":
+        c4 = bench_c4(L, torch, torch.device("cuda", 0), 1.0)
+        print(json.dumps({"profile_case": "mixed", "ms": c4["ms"]}))
+        return
     if args.profile_case == "table1-vector":
         # one vector of the Table I codes of rates 1/4 and 3/4, 10 iterations,
         # FP32 messages, twice each: the latency path (small-batch plan)
@@ -947,7 +957,8 @@ def main():
     ap.add_argument("--ref-frames-per-thread", type=int, default=4)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the quasi-cyclic, mixed-batch and weighted-BP workloads")
-    ap.add_argument("--profile-case", choices=["resident", "plain", "cluster", "table1-vector"], default=None,
+    ap.add_argument("--profile-case", choices=["resident", "plain", "cluster", "wbp", "mixed", "table1-vector"],
+                    default=None,
                     help="run one small decode (for ncu captures) instead of the benchmark")
     ap.add_argument("--frames", type=int, default=4096, help="frames of the --profile-case run")
     ap.add_argument("--fp16", action="store_true", help="binary16 messages in the plain or cluster --profile-case run")

@@ -207,3 +207,31 @@ def test_table1_code_rows_of_12(L):
     rloss, rgw, rgR, _ = wbp_ref.loss_and_grads(wl.code, wl.llr.astype(np.float64), wts.astype(np.float64), wl.cw)
     assert abs(loss - rloss) <= 1e-5 * abs(rloss) + 1e-7
     _check_grads(((gw, rgw), (gR, rgR)))
+
+
+@pytest.mark.parametrize("F", [1, 37])
+def test_irregular_code_and_ragged_batch(L, F):
+    """Rows of 3 to 7 edges and columns of 1 to 4 (a lifted quasi-cyclic code):
+    every row is shorter than the kernel's width of 8 and takes the guarded
+    path (the regular codes above take the unguarded one), and a batch
+    that is not a multiple of the frames a thread takes leaves padding frames
+    beside real ones.  Unit weights give the plain decoder's bits, random
+    weights the oracle's forward, the adjoint the FP64 reference gradient."""
+    wl = workload("qc_irregular_512", F, 2.5, seed=96)
+    c = dev_code(L, "qc_irregular_512")
+    rows = np.diff(wl.code.row_ptr)
+    assert rows.max() < 8 and rows.min() < rows.max()
+    llr = torch.from_numpy(wl.llr).cuda()
+    post = L.weighted_bp(c, llr, torch.ones((8, c.nnz), dtype=torch.float32, device="cuda"))
+    ref = L.decode(c, llr, max_iters=8, schedule="plain")
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(post.cpu().numpy(), ref.post.cpu().numpy())
+    T = 5
+    wts = _weights(T, c.nnz, seed=97)
+    post = L.weighted_bp(c, llr, torch.from_numpy(wts).cuda())
+    oref = oracle.decode(wl.code, wl.llr, iters=T, weights=wts.astype(np.float64))
+    assert llr_close(post.cpu().numpy(), oref.post).all()
+    loss, gw, gR = _gpu_loss_grads(L, c, wl.llr, wts, wl.cw)
+    rloss, rgw, rgR, _ = wbp_ref.loss_and_grads(wl.code, wl.llr.astype(np.float64), wts.astype(np.float64), wl.cw)
+    assert abs(loss - rloss) <= 1e-5 * abs(rloss) + 1e-7
+    _check_grads(((gw, rgw), (gR, rgR)))
