@@ -244,6 +244,12 @@ typedef struct ldpc_mixed ldpc_mixed;
 
 #define LDPC_MIXED_ORDER_LARGEST_FIRST 0 /* work on codes with most edges first */
 #define LDPC_MIXED_ORDER_GIVEN 1         /* codes in the order given */
+/* (In both orders the codes are then grouped by shape class -- row weight
+ * and, with binary16 messages, plane size -- which the plan decodes with one
+ * kernel each; the classes after the first run on streams the plan owns,
+ * forked from and joined back to the caller's stream with events, so a call
+ * stays one capturable sequence.  A plan must not be used by two host
+ * threads at once.) */
 
 typedef struct {
     int32_t order;           /* LDPC_MIXED_ORDER_* */

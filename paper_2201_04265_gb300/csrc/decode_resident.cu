@@ -28,409 +28,11 @@
 // place and, for early stop, evaluates the syndrome of the previous hard
 // decisions), barrier, bit pass (L_v = R_v + the bit's messages in ascending
 // edge order), barrier.
-#include <algorithm>
-
-#include "check_math.cuh"
-#include "ldpc_internal.h"
+#include "mixed_core.cuh"
+#include "resident_core.cuh"
 
 namespace ldpc {
 namespace {
-
-constexpr int kResVPT = 16;       // bits per thread
-constexpr int kResMaxThreads = 512;
-constexpr size_t kSmemLimit = 226 * 1024;  // dynamic shared memory per CTA we allow ourselves
-constexpr int kResSlots = 4;      // message slots per bit (column degree <= 4)
-constexpr int kResSlotsWide = 9;  // ... for the wide-column instances (degree <= 9)
-constexpr uint32_t kNoSlot = 0xFFFFu;
-
-// Row shapes: padded row degree and checks per thread (about 48 edges/thread).
-struct Shape {
-    int dc, cpt;
-};
-constexpr Shape kShapes[] = {{6, 8}, {9, 6}, {12, 4}, {16, 3}};
-
-struct ResArgs {
-    const float *llr;
-    int32_t F, n, npad, m, NW, T_iters, early_stop;
-    float clip2;
-    const uint32_t *edges;  // [CPT * DCW][T]
-    float *post;
-    uint32_t *hard;
-    int32_t *iters;
-    uint8_t *ok;
-    unsigned *counter;
-};
-
-// 32-bit shared-memory accesses (addresses in the shared window).  Stores
-// are volatile and clobber memory, so they keep their order with each other
-// and with the barriers.  Loads are plain (not volatile) asm: the compiler may
-// schedule them early, which the passes allow because within a pass no
-// location is both written and read by different accesses (each message
-// belongs to one check, and L or R are only read).  A load may not move
-// across a barrier: its address is derived from the plane bases, which are
-// redefined after every barrier (Smem::fence).
-__device__ __forceinline__ float lds_f(uint32_t a) {
-    float v;
-    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ uint32_t lds_u(uint32_t a) {
-    uint32_t v;
-    asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ void sts_f(uint32_t a, float v) {
-    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
-}
-__device__ __forceinline__ void sts_u(uint32_t a, uint32_t v) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-
-// Planar shared-memory layout of one frame group (see the file comment):
-// NE message planes, then G planes of totals L, then (regular codes) G planes
-// of channel LLRs R.  Regular codes (three edges per bit) need three message
-// planes and keep R on chip, which frees the registers that would hold it.
-// Regular codes keep a row of 32 spare words right after the message planes:
-// a thread's unused check slots point there (slot NE P + lane), so every
-// thread runs all its check slots without a branch; such a dummy check reads
-// real totals (bits 0..31), writes only its spare word, and is left out of
-// every syndrome.
-constexpr uint32_t kDummyBytes = 128;
-
-template <bool REG, int NSL = kResSlots>
-struct Planes {
-    static constexpr int NE = REG ? 3 : NSL;
-    static constexpr bool RSM = REG;
-};
-
-// PL > 0: planes of 2^PL words known at compile time, so that every plane
-// offset is an immediate of the shared-memory instruction and one base
-// register serves all planes of a bit; PL = 0: the plane size is a run-time
-// value.
-template <class MsgT, int G, bool REG, int PL = 0, int NSL = kResSlots>
-struct Smem {
-    static constexpr int NE = Planes<REG, NSL>::NE;  // message planes
-    uint32_t e0;      // shared address of message plane 0
-    uint32_t l0_;     // shared address of the first total plane (PL = 0)
-    uint32_t plane_;  // bytes per plane, 4 P (PL = 0)
-    uint32_t pmask_;  // P - 1 (PL = 0)
-    __device__ uint32_t plane() const {
-        if constexpr (PL > 0) return 4u << PL;
-        else return plane_;
-    }
-    __device__ uint32_t pmask() const {
-        if constexpr (PL > 0) return (1u << PL) - 1u;
-        else return pmask_;
-    }
-    __device__ uint32_t l0() const {
-        if constexpr (PL > 0) return e0 + NE * (4u << PL) + (REG ? kDummyBytes : 0);
-        else return l0_;
-    }
-    __device__ uint32_t eaddr(uint32_t s) const { return e0 + 4u * s; }
-    __device__ uint32_t dummy_slot() const { return NE * (pmask() + 1u); }
-    __device__ uint32_t laddr(uint32_t s, int i) const { return l0() + i * plane() + 4u * (s & pmask()); }
-    __device__ uint32_t eb(int v, int r) const { return e0 + r * plane() + 4u * v; }
-    __device__ uint32_t lb(int v, int i) const { return l0() + i * plane() + 4u * v; }
-    __device__ uint32_t rb(int v, int i) const { return l0() + (G + i) * plane() + 4u * v; }
-    // after a barrier: the bases become new values to the compiler, so no
-    // shared load of the next pass can be placed before the barrier
-    __device__ void fence() { asm volatile("" : "+r"(e0), "+r"(l0_)); }
-};
-
-template <class MsgT, int G, bool REG, int NSL = kResSlots>
-__host__ __device__ __forceinline__ size_t group_bytes(int npad) {
-    return (size_t)(Planes<REG, NSL>::NE + G + (Planes<REG, NSL>::RSM ? G : 0)) * 4u * npad + (REG ? kDummyBytes : 0);
-}
-
-__device__ __forceinline__ uint32_t slot_of(const uint32_t *w, int j) {
-    return (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xFFFFu);
-}
-
-// Check pass over the thread's checks, rows of exactly DC edges (REG) or of
-// at most DC edges with unused slots marked kNoSlot.  Updates the messages in
-// place.  With SYN, also returns bit i set when frame i has a check that the
-// hard decisions z = [L >= 0] (L as left by the last bit pass) do not satisfy.
-template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, class SM>
-__device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                               const SM &sm, float clip2) {
-    using EV = EVec<MsgT, G>;
-    using LV = Lanes<G>;
-    using V = typename LV::T;
-    const V zero = LV::splat(0.f);
-    uint32_t zacc[G];
-#pragma unroll
-    for (int i = 0; i < G; ++i) zacc[i] = 0;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        if (!REG && (idx[k][0] & 0xFFFFu) == kNoSlot) continue;  // no check in this slot
-        uint32_t slot[DC];
-#pragma unroll
-        for (int j = 0; j < DC; ++j) slot[j] = slot_of(idx[k], j);
-        V u[DC];
-        uint32_t xbits[DC][G], sacc[G], zsgn[G];
-        int d = 0;
-#pragma unroll
-        for (int i = 0; i < G; ++i) sacc[i] = zsgn[i] = 0;
-#pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            if (REG || slot[j] != kNoSlot) {
-                ++d;
-                float Lf[G], uf[G];
-#pragma unroll
-                for (int i = 0; i < G; ++i) Lf[i] = lds_f(sm.laddr(slot[j], i));
-                const V x = EV::sub_from(LV::make(Lf), lds_u(sm.eaddr(slot[j])));  // Eq. 6 rearranged
-#pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    if (SYN) zsgn[i] ^= __float_as_uint(Lf[i]);  // bit 31: parity of [L < 0]
-                    xbits[j][i] = __float_as_uint(LV::get(x, i));
-                    sacc[i] ^= xbits[j][i];
-                    uf[i] = ex2_approx(-fminf(fabsf(LV::get(x, i)), clip2));
-                }
-                u[j] = LV::make(uf);
-            } else {
-                u[j] = zero;  // identity for the pair products
-#pragma unroll
-                for (int i = 0; i < G; ++i) xbits[j][i] = 0u;
-            }
-        }
-        // parity of z = [L >= 0] over the row = d + parity of [L < 0] (the bit
-        // pass leaves no -0, so the sign bit is exactly [L < 0])
-        const bool real = !REG || slot[0] < sm.dummy_slot();
-        if (SYN && real)
-#pragma unroll
-            for (int i = 0; i < G; ++i) zacc[i] |= (zsgn[i] >> 31) ^ (uint32_t)(d & 1);
-        // (-1)^d folded into the accumulated sign bit
-#pragma unroll
-        for (int i = 0; i < G; ++i) sacc[i] ^= (uint32_t)(d & 1) << 31;
-        EvOdV<G> loo[DC];  // leave-one-out pairs
-        evod_leave_one_out<G, DC>(u, loo);
-#pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            if (REG || slot[j] != kNoSlot) {
-                float rc[G], mag[G];
-                uint32_t sgn[G];
-#pragma unroll
-                for (int i = 0; i < G; ++i) rc[i] = rcp_approx(LV::get(loo[j].o, i));
-                const V ratio = LV::mul(loo[j].e, LV::make(rc));
-#pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    mag[i] = fminf(lg2_approx(LV::get(ratio, i)), clip2);
-                    sgn[i] = sacc[i] ^ xbits[j][i];
-                }
-                sts_u(sm.eaddr(slot[j]), EV::signed_word(mag, sgn));
-            }
-        }
-    }
-    uint32_t bad = 0;
-    if (SYN)
-#pragma unroll
-        for (int i = 0; i < G; ++i) bad |= (zacc[i] & 1u) << i;
-    return bad;
-}
-
-// Syndrome of z = [L >= 0] over the thread's checks (no message update).
-template <class MsgT, int G, int DC, int CPT, bool REG, class SM>
-__device__ __forceinline__ uint32_t syndrome_pass(const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                                  const SM &sm) {
-    uint32_t bad = 0;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        uint32_t par = 0;
-#pragma unroll
-        for (int j = 0; j < DC; ++j) {
-            const uint32_t s = slot_of(idx[k], j);
-            if (s == kNoSlot || (REG && s >= sm.dummy_slot())) continue;
-#pragma unroll
-            for (int i = 0; i < G; ++i) par ^= (uint32_t)(lds_f(sm.laddr(s, i)) >= 0.f) << i;
-        }
-        bad |= par;  // a check with odd parity is unsatisfied
-    }
-    return bad;
-}
-
-// Bit pass (Eq. 7): L_v = R_v + the bit's messages in ascending edge order;
-// frames not in `active` keep their L_v.  REG codes have exactly three edges
-// per bit and R on chip; otherwise all four planes are summed (unused slots
-// hold 0) and R comes from registers.
-template <class MsgT, int G, bool REG, bool SYN, int NR, class SM>
-__device__ __forceinline__ void bit_pass(const float (&R)[NR][G], const SM &sm, int n,
-                                         int tid, int T, uint32_t active) {
-    using EV = EVec<MsgT, G>;
-    using LV = Lanes<G>;
-    constexpr int NS = SM::NE;
-#pragma unroll
-    for (int k = 0; k < kResVPT; ++k) {
-        const int v = tid + k * T;
-        if (v < n) {
-            float r[G];
-#pragma unroll
-            for (int i = 0; i < G; ++i) r[i] = REG ? lds_f(sm.rb(v, i)) : R[REG ? 0 : k][i];
-            typename LV::T L = LV::make(r);
-#pragma unroll
-            for (int q = 0; q < NS; ++q) L = EV::add_to(L, lds_u(sm.eb(v, q)));
-            if (SYN) L = LV::add(L, LV::splat(0.f));  // no -0: z = [L >= 0] by sign
-#pragma unroll
-            for (int i = 0; i < G; ++i)
-                if ((active >> i) & 1u) sts_f(sm.lb(v, i), LV::get(L, i));
-        }
-    }
-}
-
-// A group of threads decoding one frame group: the whole CTA ...
-struct BlockTeam {
-    __device__ int tid() const { return threadIdx.x; }
-    __device__ int size() const { return blockDim.x; }
-    __device__ void sync() const { __syncthreads(); }
-    __device__ int any(int p) const { return __syncthreads_or(p); }
-};
-
-// ... or a warp-aligned slice of it with its own named barrier (id >= 1);
-// a one-warp team synchronises with warp primitives.
-struct SubTeam {
-    int base, count, bar_id;
-    __device__ int tid() const { return (int)threadIdx.x - base; }
-    __device__ int size() const { return count; }
-    __device__ void sync() const {
-        if (count == 32)
-            __syncwarp();
-        else
-            asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(count) : "memory");
-    }
-    __device__ int any(int p) const {
-        if (count == 32) return __any_sync(0xffffffffu, p);
-        int r;
-        asm volatile(
-            "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
-            "bar.red.or.pred q, %2, %3, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
-            : "=r"(r)
-            : "r"(p), "r"(bar_id), "r"(count)
-            : "memory");
-        return r;
-    }
-};
-
-// Where the G frames of a group come from and go to (null llr = no frame).
-template <int G>
-struct ResIO {
-    const float *llr_[G];
-    float *post_[G];
-    uint32_t *hard_[G];
-    int32_t *iters_[G];
-    uint8_t *ok_[G];
-    __device__ bool exists(int i) const { return llr_[i] != nullptr; }
-    __device__ const float *llr(int i) const { return llr_[i]; }
-    __device__ float *post(int i) const { return post_[i]; }
-    __device__ uint32_t *hard(int i) const { return hard_[i]; }
-    __device__ int32_t *iters(int i) const { return iters_[i]; }
-    __device__ uint8_t *ok(int i) const { return ok_[i]; }
-};
-
-// Decodes one group of G frames with the team's threads: load R, iterate
-// (check pass, bit pass), final syndrome, outputs.  Ends with a team barrier.
-template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, class Team, class IO, class SM>
-__device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&idx)[CPT][(DC + 1) / 2],
-                                             const SM &sm_in, int n, int npad,
-                                             const IO &io, int T_iters, float clip2) {
-    SM sm = sm_in;  // local copy: its bases are fenced at every barrier
-    const int tid = tm.tid(), T = tm.size();
-    const int lane = threadIdx.x & 31;
-    uint32_t exists = 0;
-#pragma unroll
-    for (int i = 0; i < G; ++i) exists |= (uint32_t)io.exists(i) << i;
-
-    // channel LLRs (log2 units) into shared memory (REG) or registers, and
-    // L_v = R_v; messages 0
-    constexpr int NR = REG ? 1 : kResVPT;
-    float R[NR][G];
-#pragma unroll
-    for (int k = 0; k < kResVPT; ++k) {
-        const int v = tid + k * T;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const float r = (v < n && ((exists >> i) & 1u)) ? io.llr(i)[v] * kLog2e : 0.f;
-            if (!REG) R[REG ? 0 : k][i] = r;
-            if (v < n) {
-                sts_f(sm.lb(v, i), r);
-                if (REG) sts_f(sm.rb(v, i), r);
-            }
-        }
-    }
-    for (int w = tid; w < SM::NE * npad; w += T) sts_u(sm.e0 + 4u * w, 0u);
-    { tm.sync(); sm.fence(); }
-
-    uint32_t active = exists, okm = 0;
-    int it_done[G];
-#pragma unroll
-    for (int i = 0; i < G; ++i) it_done[i] = 0;
-    for (int t = 1; t <= T_iters; ++t) {
-        if (SYN && t >= 2) {
-            const uint32_t bad = check_pass<MsgT, G, DC, CPT, REG, true>(idx, sm, clip2);
-#pragma unroll
-            for (int i = 0; i < G; ++i) {
-                const int any_bad = tm.any((int)((bad >> i) & 1u));
-                if (((active >> i) & 1u) && !any_bad) {  // z^(t-1) satisfies H z = 0
-                    active &= ~(1u << i);
-                    it_done[i] = t - 1;
-                    okm |= 1u << i;
-                }
-            }
-            sm.fence();
-            if (!active) break;
-        } else {
-            check_pass<MsgT, G, DC, CPT, REG, false>(idx, sm, clip2);
-            { tm.sync(); sm.fence(); }
-        }
-        bit_pass<MsgT, G, REG, SYN>(R, sm, n, tid, T, active);
-        { tm.sync(); sm.fence(); }
-    }
-    if (active) {  // frames that ran every iteration: syndrome of the final z
-        const uint32_t bad = syndrome_pass<MsgT, G, DC, CPT, REG>(idx, sm);
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const int any_bad = tm.any((int)((bad >> i) & 1u));
-            if ((active >> i) & 1u) {
-                it_done[i] = T_iters;
-                if (!any_bad) okm |= 1u << i;
-            }
-        }
-        sm.fence();
-    }
-    // outputs: total LLRs (natural units), packed hard decisions, counts
-#pragma unroll
-    for (int k = 0; k < kResVPT; ++k) {
-        const int v = tid + k * T;
-        const int v0 = v - lane;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const float L = v < n ? lds_f(sm.lb(v, i)) : 0.f;
-            const uint32_t word = __ballot_sync(0xffffffffu, v < n && L >= 0.f);
-            if ((exists >> i) & 1u) {
-                float *post = io.post(i);
-                uint32_t *hard = io.hard(i);
-                if (post && v < n) post[v] = T_iters == 0 ? io.llr(i)[v] : L * kLn2;
-                if (hard && lane == 0 && v0 < n) hard[v0 >> 5] = word;
-            }
-        }
-    }
-    if (tid == 0)
-#pragma unroll
-        for (int i = 0; i < G; ++i)
-            if ((exists >> i) & 1u) {
-                if (int32_t *it = io.iters(i)) *it = it_done[i];
-                if (uint8_t *okp = io.ok(i)) *okp = (uint8_t)((okm >> i) & 1u);
-            }
-    { tm.sync(); sm.fence(); }
-}
-
-template <class MsgT, int G, bool REG, int PL = 0, int NSL = kResSlots>
-__device__ __forceinline__ Smem<MsgT, G, REG, PL, NSL> smem_at(unsigned char *base, int npad) {
-    Smem<MsgT, G, REG, PL, NSL> sm;
-    sm.e0 = (uint32_t)__cvta_generic_to_shared(base);
-    sm.plane_ = 4u * (uint32_t)npad;
-    sm.pmask_ = (uint32_t)npad - 1u;
-    sm.l0_ = sm.e0 + Planes<REG, NSL>::NE * sm.plane_ + (REG ? kDummyBytes : 0);
-    return sm;
-}
 
 template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, int PL = 0, int NSL = kResSlots>
 __global__ void __launch_bounds__(kResMaxThreads)
@@ -752,31 +354,6 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
 namespace ldpc {
 namespace {
 
-constexpr int kMixThreads = 512;
-
-struct MixedDesc {
-    int32_t n, npad, dc, team, teams, code;
-    const uint32_t *edges;  // [cpt * DCW][team]
-};
-
-struct MixedArgs {
-    const MixedDesc *desc;      // by work-order position
-    int32_t ncodes;
-    const unsigned *item_off;   // [ncodes + 1], by position
-    const unsigned *start;      // [ncodes], by code: first slot in `sorted`
-    const unsigned *count;      // [ncodes], by code
-    const int32_t *sorted;      // frame indices grouped by code
-    const int64_t *llr_off, *hard_off;
-    const float *llr;
-    float *post;
-    uint32_t *hard;
-    int32_t *iters;
-    uint8_t *ok;
-    unsigned *counter;
-    int32_t T_iters, gpi;
-    float clip2;
-};
-
 __global__ void mixed_count(const int32_t *__restrict__ frame_code, int32_t F, int32_t ncodes,
                             unsigned *__restrict__ count, int32_t *__restrict__ iters,
                             uint8_t *__restrict__ ok) {
@@ -881,83 +458,17 @@ __global__ void __launch_bounds__(512) mixed_sort(const unsigned *__restrict__ s
         if (out[r] >= 0) sorted[st + rank[r]] = out[r];
 }
 
-// Not inlined: each row shape gets its own register allocation instead of
-// the union of all three inside one kernel body.
-template <int G>
-struct MixIO {
-    const MixedArgs &a;
-    unsigned first, cnt, st;  // group's first index in the code's bucket
-    __device__ bool exists(int i) const { return first + i < cnt; }
-    __device__ int f(int i) const { return a.sorted[st + first + i]; }
-    __device__ const float *llr(int i) const { return a.llr + a.llr_off[f(i)]; }
-    __device__ float *post(int i) const { return a.post ? a.post + a.llr_off[f(i)] : nullptr; }
-    __device__ uint32_t *hard(int i) const { return a.hard ? a.hard + a.hard_off[f(i)] : nullptr; }
-    __device__ int32_t *iters(int i) const { return a.iters ? a.iters + f(i) : nullptr; }
-    __device__ uint8_t *ok(int i) const { return a.ok ? a.ok + f(i) : nullptr; }
-};
-
-// Not inlined: each row shape gets its own register allocation instead of
-// sharing one with the other two shapes in the kernel body.
-template <class MsgT, int G, int DC, int CPT, bool SYN>
-__device__ __noinline__ void mixed_run(const SubTeam &tm, const MixedDesc &d, const MixedArgs &a,
-                                          unsigned char *base, unsigned local) {
-    constexpr int DCW = (DC + 1) / 2;
-    uint32_t idx[CPT][DCW];
-#pragma unroll
-    for (int k = 0; k < CPT; ++k)
-#pragma unroll
-        for (int w = 0; w < DCW; ++w) idx[k][w] = __ldg(&d.edges[(size_t)(k * DCW + w) * d.team + tm.tid()]);
-    const Smem<MsgT, G, true> sm = smem_at<MsgT, G, true>(base, d.npad);
-    const unsigned cnt = a.count[d.code], st = a.start[d.code];
-    const int team = tm.base / d.team;
-    for (int gi = 0; gi < a.gpi; ++gi) {
-        const unsigned grp = (local * a.gpi + gi) * d.teams + team;
-        if ((size_t)grp * G >= cnt) break;
-        const MixIO<G> io{a, grp * G, cnt, st};
-        decode_group<MsgT, G, DC, CPT, true, SYN>(tm, idx, sm, d.n, d.npad, io, a.T_iters, a.clip2);
-    }
-}
-
-template <class MsgT, int G, bool SYN>
-__global__ void __launch_bounds__(kMixThreads)
-mixed_kernel(MixedArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ unsigned s_item;
-    const unsigned total = a.item_off[a.ncodes];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
-        __syncthreads();
-        const unsigned item = s_item;
-        __syncthreads();
-        if (item >= total) break;
-        int p = 0;
-        while (item >= a.item_off[p + 1]) ++p;
-        const MixedDesc d = a.desc[p];
-        const int team = threadIdx.x / d.team;
-        if (team < d.teams) {
-            const SubTeam tm{team * d.team, d.team, 1 + team};
-            unsigned char *base = smem_raw + (size_t)team * group_bytes<MsgT, G, true>(d.npad);
-            const unsigned local = item - a.item_off[p];
-            switch (d.dc) {
-                case 6: mixed_run<MsgT, G, 6, 8, SYN>(tm, d, a, base, local); break;
-                case 9: mixed_run<MsgT, G, 9, 6, SYN>(tm, d, a, base, local); break;
-                case 12: mixed_run<MsgT, G, 12, 4, SYN>(tm, d, a, base, local); break;
-                default: break;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-using MixedFn = void (*)(MixedArgs);
-
-MixedFn pick_mixed(bool fp16, bool syn) {
-    if (fp16) return syn ? mixed_kernel<__half, 2, true> : mixed_kernel<__half, 2, false>;
-    return syn ? mixed_kernel<float, 1, true> : mixed_kernel<float, 1, false>;
-}
 
 }  // namespace
 }  // namespace ldpc
+
+// A shape class of a plan: the codes with one row weight and (binary16
+// messages, planes of 2^10..2^13 words) one plane size, decoded by one kernel
+// instance; in work order they hold the positions [pb, pe).
+struct MixedClass {
+    int dc = 0, pl = 0, pb = 0, pe = 0;
+    size_t smem = 0;
+};
 
 struct ldpc_mixed {
     int32_t ncodes = 0;
@@ -968,27 +479,71 @@ struct ldpc_mixed {
     std::vector<uint32_t *> tables;           // device slot tables, per code
     ldpc::MixedDesc *d_desc = nullptr;        // device, in work order
     int32_t *d_nbits = nullptr;               // device, n of each code (by code index)
-    size_t smem = 0;
     ldpc_mixed_config cfg{0, 1, 1};
     int32_t desc_order = -1;                  // cfg.order the device array holds
+    std::vector<MixedClass> classes;          // in work order (for desc_order)
+    // classes after the first run on these streams, forked from and joined
+    // to the caller's stream by events
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
 };
 
 namespace ldpc {
 namespace {
 
+// Plane-size exponent of a code's kernel instance (0: size at run time).
+int mixed_plane_log(const MixedDesc &d, bool fp16) {
+    if (!fp16) return 0;
+    for (int pl = 10; pl <= 13; ++pl)
+        if (d.npad == (1 << pl)) return pl;
+    return 0;
+}
+
+// Work order: the codes (largest first, or as given), then grouped by shape
+// class with the classes in the order of their first code, so that each
+// class is one run of positions.
 int upload_order(ldpc_mixed *p, int32_t order) {
     std::vector<MixedDesc> d(p->host_desc);
     if (order == LDPC_MIXED_ORDER_LARGEST_FIRST)
         std::stable_sort(d.begin(), d.end(), [&](const MixedDesc &a, const MixedDesc &b) {
             return p->codes[a.code]->nnz > p->codes[b.code]->nnz;
         });
+    std::vector<std::pair<int, int>> keys;  // (dc, pl) in order of first appearance
+    auto key_of = [&](const MixedDesc &x) { return std::make_pair(x.dc, mixed_plane_log(x, p->fp16)); };
+    for (const MixedDesc &x : d)
+        if (std::find(keys.begin(), keys.end(), key_of(x)) == keys.end()) keys.push_back(key_of(x));
+    auto rank = [&](const MixedDesc &x) { return std::find(keys.begin(), keys.end(), key_of(x)) - keys.begin(); };
+    std::stable_sort(d.begin(), d.end(), [&](const MixedDesc &a, const MixedDesc &b) { return rank(a) < rank(b); });
+    std::vector<MixedClass> cls(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) {
+        cls[k].dc = keys[k].first;
+        cls[k].pl = keys[k].second;
+        cls[k].pb = (int)d.size();
+    }
+    for (int pos = 0; pos < (int)d.size(); ++pos) {
+        MixedClass &c = cls[rank(d[pos])];
+        c.pb = std::min(c.pb, pos);
+        c.pe = pos + 1;
+        c.smem = std::max(c.smem, (size_t)d[pos].teams * res_smem(p->codes[d[pos].code], p->fp16, true));
+    }
     LDPC_TRY_CUDA(cudaMemcpy(p->d_desc, d.data(), sizeof(MixedDesc) * d.size(), cudaMemcpyHostToDevice));
+    p->classes = cls;
     p->desc_order = order;
     return LDPC_OK;
 }
 
+MixedFn mixed_fn(int dc, bool fp16, bool syn, int pl) {
+    switch (dc) {
+        case 6: return mixed_fn_rows6(fp16, syn, pl);
+        case 9: return mixed_fn_rows9(fp16, syn, pl);
+        case 12: return mixed_fn_rows12(fp16, syn, pl);
+        default: return nullptr;
+    }
+}
+
 struct MixedWs {
-    unsigned *count, *fill, *start, *item_off, *counter;
+    unsigned *count, *fill, *start, *item_off, *counter;  // counter: one per shape class
     int32_t *sorted;
     float *score;
 };
@@ -1004,7 +559,7 @@ size_t mixed_layout(int32_t ncodes, int32_t F, MixedWs *w, void *base) {
     const size_t oF = take(sizeof(unsigned) * ncodes);
     const size_t oS = take(sizeof(unsigned) * ncodes);
     const size_t oI = take(sizeof(unsigned) * (ncodes + 1));
-    const size_t oK = take(sizeof(unsigned));
+    const size_t oK = take(sizeof(unsigned) * kMixMaxClasses);
     const size_t oX = take(sizeof(int32_t) * std::max(F, 1));
     const size_t oQ = take(sizeof(float) * std::max(F, 1));
     if (w && base) {
@@ -1067,7 +622,6 @@ int ldpc_mixed_create(const ldpc_code *const *codes, int32_t ncodes, int32_t msg
         if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMemcpy(mixed slot table)"));
         p->codes.push_back(c);
         p->host_desc.push_back(MixedDesc{c->n, pad_bits(c), sh->dc, team, teams, i, dt});
-        p->smem = std::max(p->smem, (size_t)teams * tb);
     }
     cudaError_t err = dev_malloc((void **)&p->d_desc, sizeof(MixedDesc) * ncodes);
     if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMalloc(mixed descriptors)"));
@@ -1081,6 +635,21 @@ int ldpc_mixed_create(const ldpc_code *const *codes, int32_t ncodes, int32_t msg
     }
     int st = upload_order(p, p->cfg.order);
     if (st != LDPC_OK) return cleanup(st);
+    if (p->classes.size() > (size_t)kMixMaxClasses) return cleanup(fail(LDPC_ENOTSUP, "too many shape classes"));
+    if (p->classes.size() > 1) {
+        err = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+        if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaEventCreate(mixed fork)"));
+        for (size_t k = 1; k < p->classes.size(); ++k) {
+            cudaStream_t cs = nullptr;
+            err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaStreamCreate(mixed class)"));
+            p->streams.push_back(cs);
+            cudaEvent_t ev = nullptr;
+            err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaEventCreate(mixed join)"));
+            p->joins.push_back(ev);
+        }
+    }
     *out = p;
     return LDPC_OK;
 }
@@ -1090,6 +659,9 @@ void ldpc_mixed_destroy(ldpc_mixed *p) {
     for (uint32_t *t : p->tables) cudaFree(t);
     if (p->d_desc) cudaFree(p->d_desc);
     if (p->d_nbits) cudaFree(p->d_nbits);
+    for (cudaStream_t cs : p->streams) cudaStreamDestroy(cs);
+    for (cudaEvent_t ev : p->joins) cudaEventDestroy(ev);
+    if (p->fork) cudaEventDestroy(p->fork);
     delete p;
 }
 
@@ -1136,7 +708,7 @@ int ldpc_decode_mixed(const ldpc_mixed *p, const int32_t *d_frame_code, const in
     cudaStream_t s = (cudaStream_t)stream;
     const int G = p->fp16 ? 2 : 1;
     LDPC_TRY_CUDA(cudaMemsetAsync(w.count, 0, sizeof(unsigned) * p->ncodes, s));
-    LDPC_TRY_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned), s));
+    LDPC_TRY_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned) * kMixMaxClasses, s));
     const unsigned fb = (unsigned)ceil_div(F, 256);
     mixed_count<<<fb, 256, 0, s>>>(d_frame_code, F, p->ncodes, w.count, d_iters, d_ok);
     mixed_offsets<<<1, 32, 0, s>>>(w.count, p->d_desc, p->ncodes, G, p->cfg.groups_per_item, w.start,
@@ -1146,11 +718,8 @@ int ldpc_decode_mixed(const ldpc_mixed *p, const int32_t *d_frame_code, const in
                                                           w.score);
     mixed_sort<<<(unsigned)p->ncodes, 512, 0, s>>>(w.start, w.count, w.score, w.sorted);
     const bool syn = early_stop && max_iters >= 2;
-    MixedFn fn = pick_mixed(p->fp16, syn);
-    int sms = 0, per_sm = 0;
+    int sms = 0;
     LDPC_TRY(sm_count(&sms));
-    LDPC_TRY(kernel_setup((const void *)fn, kMixThreads, p->smem, &per_sm));
-    if (per_sm < 1) return fail(LDPC_ENOTSUP, "mixed kernel cannot be resident");
     MixedArgs a;
     a.desc = p->d_desc;
     a.ncodes = p->ncodes;
@@ -1165,12 +734,38 @@ int ldpc_decode_mixed(const ldpc_mixed *p, const int32_t *d_frame_code, const in
     a.hard = d_hard;
     a.iters = d_iters;
     a.ok = d_ok;
-    a.counter = w.counter;
     a.T_iters = max_iters;
     a.gpi = p->cfg.groups_per_item;
     a.clip2 = clip_log2(clip);
-    const int grid = sms * std::min(per_sm, p->cfg.ctas_per_sm);
-    fn<<<grid, kMixThreads, p->smem, s>>>(a);
+    // one persistent kernel per shape class, in work order: the first on the
+    // caller's stream, the others on the plan's streams, which wait for the
+    // steps above and are joined back; a later class's CTAs take the SMs that
+    // an earlier class's CTAs leave
+    if (p->classes.size() > 1) LDPC_TRY_CUDA(cudaEventRecord(p->fork, s));
+    for (size_t k = 0; k < p->classes.size(); ++k) {
+        const MixedClass &cl = p->classes[k];
+        MixedFn fn = mixed_fn(cl.dc, p->fp16, syn, cl.pl);
+        if (!fn) return fail(LDPC_ENOTSUP, "no mixed kernel for rows of %d", cl.dc);
+        int per_sm = 0;
+        LDPC_TRY(kernel_setup((const void *)fn, kMixThreads, cl.smem, &per_sm));
+        if (per_sm < 1) return fail(LDPC_ENOTSUP, "mixed kernel cannot be resident");
+        MixedArgs ak = a;
+        ak.pb = cl.pb;
+        ak.pe = cl.pe;
+        ak.counter = w.counter + k;
+        const int grid = sms * std::min(per_sm, p->cfg.ctas_per_sm);
+        cudaStream_t ks = s;
+        if (k > 0) {
+            ks = p->streams[k - 1];
+            LDPC_TRY_CUDA(cudaStreamWaitEvent(ks, p->fork, 0));
+        }
+        fn<<<grid, kMixThreads, cl.smem, ks>>>(ak);
+        LDPC_TRY_CUDA(cudaGetLastError());
+        if (k > 0) {
+            LDPC_TRY_CUDA(cudaEventRecord(p->joins[k - 1], ks));
+            LDPC_TRY_CUDA(cudaStreamWaitEvent(s, p->joins[k - 1], 0));
+        }
+    }
     LDPC_TRY_CUDA(cudaGetLastError());
     return LDPC_OK;
 }

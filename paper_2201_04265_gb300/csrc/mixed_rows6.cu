@@ -1,0 +1,8 @@
+// K6 mixed-batch kernels for rows of 6 edges (mixed_core.cuh).
+#include "mixed_core.cuh"
+
+namespace ldpc {
+
+MixedFn mixed_fn_rows6(bool fp16, bool syn, int pl) { return mixed_pick<6, 8>(fp16, syn, pl); }
+
+}  // namespace ldpc
