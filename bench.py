@@ -664,7 +664,7 @@ def bench_c4(L, torch, dev, xu_peak):
     """The mixed serving batch: 2000 frames whose code is drawn uniformly from
     15 random regular codes (n in {504 .. 8064} x degree pairs (3,6), (3,9),
     (3,12)), Eb/N0 ~ U[1, 4] dB per frame, early stop after at most 50
-    iterations, binary16 messages, one persistent launch (K6) replayed from a
+    iterations, binary16 messages, persistent kernels per shape class (K6) replayed from a
     CUDA graph with the autotuned configuration."""
     import ldpc_synth as S
     NS = (504, 1008, 2016, 4032, 8064)
@@ -722,7 +722,7 @@ def bench_c4(L, torch, dev, xu_peak):
                         "early stop <= 50 iterations, binary16 messages",
             "ms": round(ms, 4), "gbps": round(bits_info / (ms * 1e-3) / 1e9, 4), "frames": F,
             "mean_iterations": round(float(iters.mean()), 3), "fer": errors / F, "autotuned": cfg,
-            "graph": "one persistent launch (plus the count, offset and scatter kernels) replayed from a CUDA graph",
+            "graph": "count, offset, scatter, score and sort kernels, then one persistent kernel per shape class (row weight, plane size) on forked streams, replayed from a CUDA graph",
             "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(xu_peak, 4),
                          "unit": "Tops/s (MUFU ex2/rcp/lg2)", "frac": round(achieved / xu_peak, 4),
                          "note": "3 MUFU ops per edge and check pass actually run (early stop)"}}

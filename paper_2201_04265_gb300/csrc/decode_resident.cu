@@ -34,42 +34,6 @@
 namespace ldpc {
 namespace {
 
-template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, int PL = 0, int NSL = kResSlots>
-__global__ void __launch_bounds__(kResMaxThreads)
-resident_kernel(ResArgs a) {
-    constexpr int DCW = (DC + 1) / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem<MsgT, G, REG, PL, NSL> sm = smem_at<MsgT, G, REG, PL, NSL>(smem_raw, a.npad);
-    __shared__ int s_group;
-    const int T = blockDim.x, tid = threadIdx.x;
-    uint32_t idx[CPT][DCW];
-#pragma unroll
-    for (int k = 0; k < CPT; ++k)
-#pragma unroll
-        for (int w = 0; w < DCW; ++w) idx[k][w] = __ldg(&a.edges[(size_t)(k * DCW + w) * T + tid]);
-    const int groups = (a.F + G - 1) / G;
-    for (;;) {
-        if (tid == 0) s_group = (int)atomicAdd(a.counter, 1u);
-        __syncthreads();
-        const int grp = s_group;
-        __syncthreads();
-        if (grp >= groups) break;
-        ResIO<G> io;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const int64_t f = (int64_t)grp * G + i;
-            const bool ex = f < a.F;
-            io.llr_[i] = ex ? a.llr + f * a.n : nullptr;
-            io.post_[i] = ex && a.post ? a.post + f * a.n : nullptr;
-            io.hard_[i] = ex && a.hard ? a.hard + f * a.NW : nullptr;
-            io.iters_[i] = ex && a.iters ? a.iters + f : nullptr;
-            io.ok_[i] = ex && a.ok ? a.ok + f : nullptr;
-        }
-        decode_group<MsgT, G, DC, CPT, REG, SYN>(BlockTeam{}, idx, sm, a.n, a.npad, io, a.T_iters, a.clip2);
-    }
-}
-
-using KernelFn = void (*)(ResArgs);
 
 template <class MsgT, int G, int DC, int CPT>
 KernelFn pick_flags(bool reg, bool syn) {
@@ -77,19 +41,17 @@ KernelFn pick_flags(bool reg, bool syn) {
     return syn ? resident_kernel<MsgT, G, DC, CPT, false, true> : resident_kernel<MsgT, G, DC, CPT, false, false>;
 }
 
-// Regular (3,6) codes with binary16 messages -- the common long-code case --
-// also have instances with the plane size fixed at compile time (2^10 ..
-// 2^13 words); the results are the same bits.
-template <int PL>
-KernelFn pick_fixed_plane(bool syn) {
-    return syn ? resident_kernel<__half, 2, 6, 8, true, true, PL> : resident_kernel<__half, 2, 6, 8, true, false, PL>;
-}
-KernelFn pick_fixed(int npad, bool syn) {
-    switch (npad) {
-        case 1024: return pick_fixed_plane<10>(syn);
-        case 2048: return pick_fixed_plane<11>(syn);
-        case 4096: return pick_fixed_plane<12>(syn);
-        case 8192: return pick_fixed_plane<13>(syn);
+// Regular codes with binary16 messages -- the common long-code case -- also
+// have instances with the plane size fixed at compile time (2^10 .. 2^13
+// words); the results are the same bits.
+KernelFn pick_fixed(int dc, int npad, bool syn) {
+    int pl = 0;
+    for (int k = 10; k <= 13; ++k)
+        if (npad == (1 << k)) pl = k;
+    switch (dc) {
+        case 6: return resident_fixed_rows6(pl, syn);
+        case 9: return resident_fixed_rows9(pl, syn);
+        case 12: return resident_fixed_rows12(pl, syn);
         default: return nullptr;
     }
 }
@@ -280,7 +242,7 @@ int decode_resident(const ldpc_code *c, const float *d_llr, int32_t F, const ldp
     const bool fp16 = o->msg_fp16 != 0;
     const bool syn = o->early_stop != 0 && o->max_iters >= 2;
     KernelFn fn = nullptr;
-    if (fp16 && c->res.regular && c->res.dc_pad == 6) fn = pick_fixed(pad_bits(c), syn);
+    if (fp16 && c->res.regular) fn = pick_fixed(c->res.dc_pad, pad_bits(c), syn);
     if (c->res.dv_pad == kResSlotsWide) {
         if (c->res.dc_pad != 12) return fail(LDPC_ENOTSUP, "no wide-column resident kernel for rows of %d", c->res.dc_pad);
         fn = fp16 ? (syn ? resident_kernel<__half, 2, 12, 4, false, true, 0, kResSlotsWide>
@@ -423,39 +385,44 @@ __global__ void mixed_score(const int32_t *__restrict__ frame_code, const int64_
 // iteration, and the two frames of a binary16 group have similar quality, so a
 // group rarely waits for one slow frame.  The order changes no result.
 constexpr int kSortCap = 4096;  // larger buckets keep their arrival order
+
+// Orders one code's bucket of frames by (score, frame index) ascending: a
+// bitonic sort of 64-bit keys (the score's bits above the frame index; scores
+// are non-negative, so their bit patterns order like the values) in shared
+// memory, the bucket padded to a power of two with keys above every real one.
 __global__ void __launch_bounds__(512) mixed_sort(const unsigned *__restrict__ start,
                                                   const unsigned *__restrict__ count,
                                                   const float *__restrict__ score, int32_t *__restrict__ sorted) {
-    __shared__ float ks[kSortCap];
-    __shared__ int32_t kf[kSortCap];
+    __shared__ unsigned long long key[kSortCap];
     const int c = blockIdx.x;
     const unsigned n = count[c], st = start[c];
     if (n < 2 || n > kSortCap) return;
-    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-        kf[i] = sorted[st + i];
-        ks[i] = score[kf[i]];
-    }
-    __syncthreads();
-    int32_t out[kSortCap / 512];
-    unsigned rank[kSortCap / 512];
-#pragma unroll
-    for (int r = 0; r < kSortCap / 512; ++r) {
-        const unsigned i = threadIdx.x + 512u * r;
-        rank[r] = 0;
-        out[r] = -1;
+    unsigned P = 2;
+    while (P < n) P <<= 1;
+    for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
         if (i < n) {
-            const float si = ks[i];
-            const int32_t fi = kf[i];
-            unsigned k = 0;
-            for (unsigned j = 0; j < n; ++j) k += (ks[j] < si) || (ks[j] == si && kf[j] < fi);
-            rank[r] = k;
-            out[r] = fi;
+            const int32_t f = sorted[st + i];
+            key[i] = ((unsigned long long)__float_as_uint(score[f]) << 32) | (uint32_t)f;
+        } else {
+            key[i] = ~0ull;
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kSortCap / 512; ++r)
-        if (out[r] >= 0) sorted[st + rank[r]] = out[r];
+    for (unsigned k = 2; k <= P; k <<= 1)
+        for (unsigned j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
+                const unsigned l = i ^ j;
+                if (l > i) {
+                    const unsigned long long x = key[i], y = key[l];
+                    if ((x > y) == ((i & k) == 0)) {  // ascending where bit k of i is 0
+                        key[i] = y;
+                        key[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) sorted[st + i] = (int32_t)(uint32_t)key[i];
 }
 
 

@@ -4,7 +4,7 @@
 // A plan's codes are grouped into shape classes -- row weight and, for
 // binary16 messages with planes of 2^10..2^13 words, the plane size -- and
 // each class has its own persistent kernel, instantiated in its own
-// translation unit (mixed_rows6.cu, mixed_rows9.cu, mixed_rows12.cu).  With
+// translation unit (rows6.cu, rows9.cu, rows12.cu).  With
 // the decode of a group inlined into a kernel of one shape, the register
 // allocation is that of the single-code resident kernel; a kernel holding all
 // shapes (inlined, or as called functions) spilled inside the check pass.

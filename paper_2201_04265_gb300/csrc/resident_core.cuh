@@ -10,6 +10,29 @@
 #include "ldpc_internal.h"
 
 namespace ldpc {
+
+struct ResArgs {
+    const float *llr;
+    int32_t F, n, npad, m, NW, T_iters, early_stop;
+    float clip2;
+    const uint32_t *edges;  // [CPT * DCW][T]
+    float *post;
+    uint32_t *hard;
+    int32_t *iters;
+    uint8_t *ok;
+    unsigned *counter;
+};
+
+using KernelFn = void (*)(ResArgs);
+
+// Resident kernels with planes of 2^pl words fixed at compile time (pl =
+// 10..13) for regular codes (three edges per bit) with binary16 messages and
+// rows of 6, 9 or 12 edges; null for other pl.  Instantiated per row weight
+// in rows6.cu, rows9.cu and rows12.cu.
+KernelFn resident_fixed_rows6(int pl, bool syn);
+KernelFn resident_fixed_rows9(int pl, bool syn);
+KernelFn resident_fixed_rows12(int pl, bool syn);
+
 namespace {
 
 constexpr int kResVPT = 16;       // bits per thread
@@ -25,17 +48,6 @@ struct Shape {
 };
 constexpr Shape kShapes[] = {{6, 8}, {9, 6}, {12, 4}, {16, 3}};
 
-struct ResArgs {
-    const float *llr;
-    int32_t F, n, npad, m, NW, T_iters, early_stop;
-    float clip2;
-    const uint32_t *edges;  // [CPT * DCW][T]
-    float *post;
-    uint32_t *hard;
-    int32_t *iters;
-    uint8_t *ok;
-    unsigned *counter;
-};
 
 // 32-bit shared-memory accesses (addresses in the shared window).  Stores
 // are volatile and clobber memory, so they keep their order with each other
@@ -315,19 +327,28 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
     for (int i = 0; i < G; ++i) exists |= (uint32_t)io.exists(i) << i;
 
     // channel LLRs (log2 units) into shared memory (REG) or registers, and
-    // L_v = R_v; messages 0
+    // L_v = R_v; messages 0.  All of a thread's loads are issued before its
+    // first shared store (a store is ordered with every memory access).
+    const float *src[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) src[i] = ((exists >> i) & 1u) ? io.llr(i) : nullptr;
     constexpr int NR = REG ? 1 : kResVPT;
-    float R[NR][G];
+    float R[NR][G], Rv[kResVPT][G];
+#pragma unroll
+    for (int k = 0; k < kResVPT; ++k) {
+        const int v = tid + k * T;
+#pragma unroll
+        for (int i = 0; i < G; ++i) Rv[k][i] = (v < n && src[i]) ? src[i][v] * kLog2e : 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < kResVPT; ++k) {
         const int v = tid + k * T;
 #pragma unroll
         for (int i = 0; i < G; ++i) {
-            const float r = (v < n && ((exists >> i) & 1u)) ? io.llr(i)[v] * kLog2e : 0.f;
-            if (!REG) R[REG ? 0 : k][i] = r;
+            if (!REG) R[REG ? 0 : k][i] = Rv[k][i];
             if (v < n) {
-                sts_f(sm.lb(v, i), r);
-                if (REG) sts_f(sm.rb(v, i), r);
+                sts_f(sm.lb(v, i), Rv[k][i]);
+                if (REG) sts_f(sm.rb(v, i), Rv[k][i]);
             }
         }
     }
@@ -372,6 +393,15 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
         sm.fence();
     }
     // outputs: total LLRs (natural units), packed hard decisions, counts
+    float *post[G];
+    uint32_t *hard[G];
+    const float *in0[G];  // with no iterations the posterior is the input itself
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        post[i] = ((exists >> i) & 1u) ? io.post(i) : nullptr;
+        hard[i] = ((exists >> i) & 1u) ? io.hard(i) : nullptr;
+        in0[i] = post[i] && T_iters == 0 ? io.llr(i) : nullptr;
+    }
 #pragma unroll
     for (int k = 0; k < kResVPT; ++k) {
         const int v = tid + k * T;
@@ -380,12 +410,8 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
         for (int i = 0; i < G; ++i) {
             const float L = v < n ? lds_f(sm.lb(v, i)) : 0.f;
             const uint32_t word = __ballot_sync(0xffffffffu, v < n && L >= 0.f);
-            if ((exists >> i) & 1u) {
-                float *post = io.post(i);
-                uint32_t *hard = io.hard(i);
-                if (post && v < n) post[v] = T_iters == 0 ? io.llr(i)[v] : L * kLn2;
-                if (hard && lane == 0 && v0 < n) hard[v0 >> 5] = word;
-            }
+            if (post[i] && v < n) post[i][v] = in0[i] ? in0[i][v] : L * kLn2;
+            if (hard[i] && lane == 0 && v0 < n) hard[i][v0 >> 5] = word;
         }
     }
     if (tid == 0)
@@ -406,6 +432,52 @@ __device__ __forceinline__ Smem<MsgT, G, REG, PL, NSL> smem_at(unsigned char *ba
     sm.pmask_ = (uint32_t)npad - 1u;
     sm.l0_ = sm.e0 + Planes<REG, NSL>::NE * sm.plane_ + (REG ? kDummyBytes : 0);
     return sm;
+}
+
+template <class MsgT, int G, int DC, int CPT, bool REG, bool SYN, int PL = 0, int NSL = kResSlots>
+__global__ void __launch_bounds__(kResMaxThreads)
+resident_kernel(ResArgs a) {
+    constexpr int DCW = (DC + 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Smem<MsgT, G, REG, PL, NSL> sm = smem_at<MsgT, G, REG, PL, NSL>(smem_raw, a.npad);
+    __shared__ int s_group;
+    const int T = blockDim.x, tid = threadIdx.x;
+    uint32_t idx[CPT][DCW];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+#pragma unroll
+        for (int w = 0; w < DCW; ++w) idx[k][w] = __ldg(&a.edges[(size_t)(k * DCW + w) * T + tid]);
+    const int groups = (a.F + G - 1) / G;
+    for (;;) {
+        if (tid == 0) s_group = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int grp = s_group;
+        __syncthreads();
+        if (grp >= groups) break;
+        ResIO<G> io;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const int64_t f = (int64_t)grp * G + i;
+            const bool ex = f < a.F;
+            io.llr_[i] = ex ? a.llr + f * a.n : nullptr;
+            io.post_[i] = ex && a.post ? a.post + f * a.n : nullptr;
+            io.hard_[i] = ex && a.hard ? a.hard + f * a.NW : nullptr;
+            io.iters_[i] = ex && a.iters ? a.iters + f : nullptr;
+            io.ok_[i] = ex && a.ok ? a.ok + f : nullptr;
+        }
+        decode_group<MsgT, G, DC, CPT, REG, SYN>(BlockTeam{}, idx, sm, a.n, a.npad, io, a.T_iters, a.clip2);
+    }
+}
+
+template <int DC, int CPT>
+KernelFn resident_fixed_pick(int pl, bool syn) {
+    switch (pl) {
+        case 10: return syn ? resident_kernel<__half, 2, DC, CPT, true, true, 10> : resident_kernel<__half, 2, DC, CPT, true, false, 10>;
+        case 11: return syn ? resident_kernel<__half, 2, DC, CPT, true, true, 11> : resident_kernel<__half, 2, DC, CPT, true, false, 11>;
+        case 12: return syn ? resident_kernel<__half, 2, DC, CPT, true, true, 12> : resident_kernel<__half, 2, DC, CPT, true, false, 12>;
+        case 13: return syn ? resident_kernel<__half, 2, DC, CPT, true, true, 13> : resident_kernel<__half, 2, DC, CPT, true, false, 13>;
+        default: return nullptr;
+    }
 }
 
 }  // namespace

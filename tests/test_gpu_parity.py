@@ -296,6 +296,30 @@ def test_resident_matches_plain_bit_for_bit(L, name, fp16, early_stop):
         np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("dc,npad_log", [(6, 12), (9, 12), (9, 13), (12, 12), (12, 13)])
+@pytest.mark.parametrize("early_stop", [False, True])
+def test_resident_fixed_plane_instances_bit_for_bit(L, dc, npad_log, early_stop):
+    """Regular codes with binary16 messages and planes of 2^12 or 2^13 words
+    take the resident instances with the plane size fixed at compile time
+    (rows of 6, 9 and 12); they give the plain decoder's bits.  All-zero
+    codewords at Eb/N0 from 1 to 4 dB over the frames, so that with early
+    stop some frames stop at different iterations and some run them all."""
+    n = {12: 4032, 13: 8064}[npad_log] // dc * dc
+    h = S.random_regular(n, 3, dc, seed=60 + dc)
+    c = L.Code.from_csr_code(h)
+    F = 13
+    llr = S.bpsk_awgn_llr(np.zeros((F, n), dtype=np.uint8), np.linspace(1.0, 4.0, F), 1 - 3 / dc,
+                          S.frame_noise(F, n, 72))
+    kw = dict(max_iters=30, early_stop=early_stop, msg_fp16=True)
+    a = _gpu_decode(L, c, llr, schedule="plain", **kw)
+    b = _gpu_decode(L, c, llr, schedule="resident", **kw)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    if early_stop:
+        assert len(np.unique(a[2])) > 1
+    c.close()
+
+
 @pytest.mark.parametrize("name", ["c1_gallager_504", "reg312_2016", "qc_irregular_512",
                                   "table1_r025", "table1_r050", "table1_r075"])
 @pytest.mark.parametrize("F", [1, 37])
