@@ -453,7 +453,7 @@ def _recorded_traffic():
                 rec[k.strip()] = v.strip()
     csrc = os.path.join(ROOT, "paper_2201_04265_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("decode_resident.cu", "check_math.cuh"):
+    for name in ("resident_core.cuh", "check_math.cuh", "rows6.cu"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     if h.hexdigest()[:16] != rec.get("source_hash"):
