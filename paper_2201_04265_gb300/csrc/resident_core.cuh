@@ -73,10 +73,20 @@ __device__ __forceinline__ void sts_f(uint32_t a, float v) {
 __device__ __forceinline__ void sts_u(uint32_t a, uint32_t v) {
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
+// The two frames' values of one bit (8-byte aligned), in one access.
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+    float2 v;
+    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_f2(uint32_t a, float x, float y) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
 
 // Planar shared-memory layout of one frame group (see the file comment):
-// NE message planes, then G planes of totals L, then (regular codes) G planes
-// of channel LLRs R.  Regular codes (three edges per bit) need three message
+// NE message planes, then the totals L, then (regular codes) the channel LLRs
+// R, each a plane of P entries of G floats (the G frames of a bit adjacent,
+// so a two-frame group reads or writes a bit's pair in one 8-byte access).  Regular codes (three edges per bit) need three message
 // planes and keep R on chip, which frees the registers that would hold it.
 // Regular codes keep a row of 32 spare words right after the message planes:
 // a thread's unused check slots point there (slot NE P + lane), so every
@@ -116,10 +126,10 @@ struct Smem {
     }
     __device__ uint32_t eaddr(uint32_t s) const { return e0 + 4u * s; }
     __device__ uint32_t dummy_slot() const { return NE * (pmask() + 1u); }
-    __device__ uint32_t laddr(uint32_t s, int i) const { return l0() + i * plane() + 4u * (s & pmask()); }
+    __device__ uint32_t laddr(uint32_t s, int i) const { return l0() + 4u * (G * (s & pmask()) + i); }
     __device__ uint32_t eb(int v, int r) const { return e0 + r * plane() + 4u * v; }
-    __device__ uint32_t lb(int v, int i) const { return l0() + i * plane() + 4u * v; }
-    __device__ uint32_t rb(int v, int i) const { return l0() + (G + i) * plane() + 4u * v; }
+    __device__ uint32_t lb(int v, int i) const { return l0() + 4u * (G * v + i); }
+    __device__ uint32_t rb(int v, int i) const { return l0() + G * plane() + 4u * (G * v + i); }
     // after a barrier: the bases become new values to the compiler, so no
     // shared load of the next pass can be placed before the barrier
     __device__ void fence() { asm volatile("" : "+r"(e0), "+r"(l0_)); }
@@ -165,7 +175,13 @@ __device__ __forceinline__ uint32_t check_pass(const uint32_t (&idx)[CPT][(DC + 
                 ++d;
                 float Lf[G], uf[G];
 #pragma unroll
-                for (int i = 0; i < G; ++i) Lf[i] = lds_f(sm.laddr(slot[j], i));
+                if constexpr (G == 2) {
+                    const float2 t = lds_f2(sm.laddr(slot[j], 0));
+                    Lf[0] = t.x;
+                    Lf[G - 1] = t.y;
+                } else {
+                    for (int i = 0; i < G; ++i) Lf[i] = lds_f(sm.laddr(slot[j], i));
+                }
                 const V x = EV::sub_from(LV::make(Lf), lds_u(sm.eaddr(slot[j])));  // Eq. 6 rearranged
 #pragma unroll
                 for (int i = 0; i < G; ++i) {
@@ -229,7 +245,12 @@ __device__ __forceinline__ uint32_t syndrome_pass(const uint32_t (&idx)[CPT][(DC
             const uint32_t s = slot_of(idx[k], j);
             if (s == kNoSlot || (REG && s >= sm.dummy_slot())) continue;
 #pragma unroll
-            for (int i = 0; i < G; ++i) par ^= (uint32_t)(lds_f(sm.laddr(s, i)) >= 0.f) << i;
+            if constexpr (G == 2) {
+                const float2 t = lds_f2(sm.laddr(s, 0));
+                par ^= (uint32_t)(t.x >= 0.f) | ((uint32_t)(t.y >= 0.f) << 1);
+            } else {
+                for (int i = 0; i < G; ++i) par ^= (uint32_t)(lds_f(sm.laddr(s, i)) >= 0.f) << i;
+            }
         }
         bad |= par;  // a check with odd parity is unsatisfied
     }
@@ -251,15 +272,25 @@ __device__ __forceinline__ void bit_pass(const float (&R)[NR][G], const SM &sm, 
         const int v = tid + k * T;
         if (v < n) {
             float r[G];
+            if constexpr (REG && G == 2) {
+                const float2 t = lds_f2(sm.rb(v, 0));
+                r[0] = t.x;
+                r[G - 1] = t.y;
+            } else {
 #pragma unroll
-            for (int i = 0; i < G; ++i) r[i] = REG ? lds_f(sm.rb(v, i)) : R[REG ? 0 : k][i];
+                for (int i = 0; i < G; ++i) r[i] = REG ? lds_f(sm.rb(v, i)) : R[REG ? 0 : k][i];
+            }
             typename LV::T L = LV::make(r);
 #pragma unroll
             for (int q = 0; q < NS; ++q) L = EV::add_to(L, lds_u(sm.eb(v, q)));
             if (SYN) L = LV::add(L, LV::splat(0.f));  // no -0: z = [L >= 0] by sign
+            if (G == 2 && active == 3u) {  // both frames still running: one store
+                sts_f2(sm.lb(v, 0), LV::get(L, 0), LV::get(L, G - 1));
+            } else {
 #pragma unroll
-            for (int i = 0; i < G; ++i)
-                if ((active >> i) & 1u) sts_f(sm.lb(v, i), LV::get(L, i));
+                for (int i = 0; i < G; ++i)
+                    if ((active >> i) & 1u) sts_f(sm.lb(v, i), LV::get(L, i));
+            }
         }
     }
 }
@@ -346,10 +377,14 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             if (!REG) R[REG ? 0 : k][i] = Rv[k][i];
-            if (v < n) {
+            if (G == 1 && v < n) {
                 sts_f(sm.lb(v, i), Rv[k][i]);
                 if (REG) sts_f(sm.rb(v, i), Rv[k][i]);
             }
+        }
+        if (G == 2 && v < n) {
+            sts_f2(sm.lb(v, 0), Rv[k][0], Rv[k][G - 1]);
+            if (REG) sts_f2(sm.rb(v, 0), Rv[k][0], Rv[k][G - 1]);
         }
     }
     for (int w = tid; w < SM::NE * npad; w += T) sts_u(sm.e0 + 4u * w, 0u);
@@ -406,9 +441,18 @@ __device__ __forceinline__ void decode_group(const Team &tm, const uint32_t (&id
     for (int k = 0; k < kResVPT; ++k) {
         const int v = tid + k * T;
         const int v0 = v - lane;
+        float Lo[G];
+        if constexpr (G == 2) {
+            const float2 t = v < n ? lds_f2(sm.lb(v, 0)) : make_float2(0.f, 0.f);
+            Lo[0] = t.x;
+            Lo[G - 1] = t.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < G; ++i) Lo[i] = v < n ? lds_f(sm.lb(v, i)) : 0.f;
+        }
 #pragma unroll
         for (int i = 0; i < G; ++i) {
-            const float L = v < n ? lds_f(sm.lb(v, i)) : 0.f;
+            const float L = Lo[i];
             const uint32_t word = __ballot_sync(0xffffffffu, v < n && L >= 0.f);
             if (post[i] && v < n) post[i][v] = in0[i] ? in0[i][v] : L * kLn2;
             if (hard[i] && lane == 0 && v0 < n) hard[i][v0 >> 5] = word;
