@@ -12,12 +12,15 @@
 // memory holds, with P = n rounded up to a power of two:
 //   E[r][P]  check messages, plane r = the r-th edge of each bit (in
 //            ascending CSR edge order); half2 (both frames) or float
-//   L_i[P]   total LLR L_v of frame i (float), one plane per frame
+//   L[P][G]  total LLRs L_v of the G frames (float), a bit's G values
+//            adjacent (one 8-byte access for a two-frame group)
+//   R[P][G]  channel LLRs of regular codes, laid out like L
 // All planes have a stride that is a multiple of 32 words, so an access to
-// bit v falls in bank v mod 32.  The check schedule (schedule.cpp) groups the
-// checks of each warp and orders each check's edges so that at every step the
-// 32 lanes touch 32 distinct banks.  An edge is a 16-bit slot s = r P + v:
-// its message is at byte 4 s, its bit's totals at (4 s mod 4P) + plane base.
+// bit v falls in bank v mod 32 (bank pair v mod 16 for the 8-byte pairs).
+// The check schedule (schedule.cpp) groups the checks of each warp and orders
+// each check's edges so that at every step the 32 lanes touch 32 distinct
+// banks.  An edge is a 16-bit slot s = r P + v: its message is at byte 4 s,
+// its bit's totals at 4 G (s mod P) + the base of L.
 //
 // Thread t owns the checks of its (warp, slot) schedule groups and the bits
 // t, t+T, ...: its checks' slots are loaded once into registers from a table
