@@ -911,7 +911,7 @@ def run_profile_case(args):
         return
     if args.profile_case == "mixed":
         c4 = bench_c4(L, torch, torch.device("cuda", 0), 1.0)
-        print(json.dumps({"profile_case": "mixed", "ms": c4["ms"]}))
+        print(json.dumps({"profile_case": "mixed", "ms": c4["ms"], "autotuned": c4["autotuned"]}))
         return
     if args.profile_case == "table1-vector":
         # one vector of the Table I codes of rates 1/4 and 3/4, 10 iterations,

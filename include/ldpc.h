@@ -280,9 +280,13 @@ int ldpc_decode_mixed(const ldpc_mixed *plan, const int32_t *d_frame_code, const
                       ldpc_stream_t stream);
 
 /* Autotuner: decodes the given batch with every candidate configuration
- * (work order x groups per item x CTAs per SM), times `reps` runs of each with
- * CUDA events, keeps the fastest in the plan and returns it in *chosen.
- * Synchronises the stream; outputs hold the last run's (identical) results. */
+ * (work order x groups per item x CTAs per SM), each captured in a CUDA graph
+ * on a private stream that starts after the work queued on `stream`, and times
+ * the graph's replays with CUDA events (`reps` timed replays per candidate
+ * after an untimed one, in two passes over the candidates, the second in
+ * reverse order); keeps the one with the lowest median time in the plan and
+ * returns it in *chosen.  Returns when all its work is done; outputs hold the
+ * last replay's (identical) results.  Not to be called during a stream capture. */
 int ldpc_mixed_autotune(ldpc_mixed *plan, const int32_t *d_frame_code, const int64_t *d_llr_off,
                         const int64_t *d_hard_off, const float *d_llr, int32_t F, int32_t max_iters,
                         int32_t early_stop, float clip, float *d_post, uint32_t *d_hard,
